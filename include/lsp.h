@@ -1,0 +1,192 @@
+/*
+ * lsp.h -- C ABI of the GB300 lattice Strang-splitting TDSE library.
+ *
+ * The library time-steps the time-dependent Schroedinger equation
+ *     i gamma du/dt = -(gamma^2/2) Lap u + v u      on the d-torus [0,1)^d
+ * (Suzuki, Suryanarayana, Nuyens, arXiv:1808.06357, Sec. 1 eq. TDSE) with the
+ * Fourier pseudo-spectral method on a rank-1 or rank-r lattice (Sec. 2.1-2.2)
+ * and Strang splitting in time (Sec. 2.3-2.5, eq. StrangTDSE, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: LSP_OK (0) on success, a negative LSP_ERR_* code otherwise.
+ *   Nothing is thrown across the ABI.  lsp_strerror() names a code.
+ * - A plan owns all device memory it uses.  Input buffers are copied; the
+ *   caller keeps ownership of every pointer it passes.
+ * - "on_device" arguments: 1 = the pointer is device memory on the plan's
+ *   device, 0 = host memory (pageable or pinned).
+ * - "stream" arguments are a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream).  Calls taking a stream are asynchronous on it, except
+ *   that host-pointer transfers of lsp_get_state synchronise the stream
+ *   before returning.  Plan creation and destruction are synchronous.
+ * - One plan must not be used from two streams concurrently.
+ * - State layout: u holds physical samples u(p_kappa) at the lattice points,
+ *   kappa = sum_i kappa_i prod_{j>i} n_j (lexicographic, Sec. 2.5), as
+ *   interleaved (re, im) pairs.  Lattice point
+ *   p_kappa = (z_1 kappa_1/n_1 + ... + z_r kappa_r/n_r) mod 1 (Def. 1).
+ * - Spectral layout: bin chi = sum_i xi_i prod_{j>i} n_j with
+ *   xi_i = h . z_i mod n_i (Thm 1(iii), Sec. 2.5); the coefficient stored for
+ *   bin chi is uhat(h_chi) = (1/n) sum_kappa u_kappa exp(-2 pi i h_chi . p_kappa)
+ *   (eq. approx_uhat).
+ */
+#ifndef LSP_H
+#define LSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsp_plan_s* lsp_plan;
+typedef struct lsp_batch_s* lsp_batch;
+
+/* Status codes. */
+enum {
+  LSP_OK = 0,
+  LSP_ERR_BAD_ARG = -1,        /* invalid argument (null pointer, size, mode)                  */
+  LSP_ERR_NOT_CANONICAL = -2,  /* lattice violates Def. 1 (n_{i+1} | n_i, gcd(z_i, n_i) = 1,
+                                  n distinct points)                                         */
+  LSP_ERR_NOT_INJECTIVE = -3,  /* explicit index set violates Def. 2 or has |A| != n         */
+  LSP_ERR_TOO_LARGE = -4,      /* size beyond what the kernels support                       */
+  LSP_ERR_OOM = -5,            /* device allocation failed                                   */
+  LSP_ERR_CUDA = -6,           /* a CUDA runtime call failed                                 */
+  LSP_ERR_TIMEOUT = -7,        /* a bounded device-side wait expired; the step was abandoned */
+  LSP_ERR_UNSUPPORTED = -8     /* combination not implemented (e.g. lattice shape)           */
+};
+
+/* Precision of the state and of the butterflies. */
+enum { LSP_C64 = 1,  /* complex64: FP32 state, FP32 butterflies, FP64-reduced phases */
+       LSP_C128 = 2  /* complex128: FP64 throughout                                  */ };
+
+/* How the anti-aliasing set A(Z, n) of full cardinality n is chosen. */
+enum { LSP_AA_MINL2 = 0,    /* each bin takes a minimal-l2 representative h_chi
+                               (Lemma 4, eq. hrepresenter); computed exactly on the GPU */
+       LSP_AA_EXPLICIT = 1  /* the caller supplies all n vectors h (Def. 2)             */ };
+
+/* Space selector for lsp_get_state. */
+enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
+
+/*
+ * lsp_plan_create -- build a plan for one TDSE instance on one device.
+ *   out        receives the plan handle.
+ *   d          spatial dimension, 1 <= d <= 64.
+ *   r          lattice rank, 1 <= r <= 2 (r = 1: rank-1 lattice Lambda(z, n), Sec. 2.1;
+ *              r = 2: rank-2 lattice Lambda(Z, n) in canonical form, Def. 1).
+ *   n          r moduli n_1..n_r (host); n = prod n_i points.
+ *   Z          d*r generating-vector entries (host), row-major: Z[j*r + i] is
+ *              component j of z_i.
+ *   index_set  LSP_AA_EXPLICIT: m*d int32 entries (host), row-major, the full
+ *              anti-aliasing set (m must equal n).  LSP_AA_MINL2: NULL.
+ *   m          number of rows of index_set (0 for MINL2).
+ *   aa_mode    LSP_AA_MINL2 or LSP_AA_EXPLICIT.
+ *   prec       LSP_C64 or LSP_C128.
+ *   gamma      gamma = hbar / sqrt(mass) > 0 (Sec. 1).
+ *   device     CUDA device ordinal.
+ * Errors: BAD_ARG, NOT_CANONICAL, NOT_INJECTIVE, TOO_LARGE, OOM, CUDA,
+ * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
+ * The state starts at zero and the potential at v = 0.
+ */
+int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
+                    const int32_t* index_set, int64_t m, int aa_mode, int prec,
+                    double gamma, int device);
+
+/* Release every resource of the plan (synchronises the device). NULL is a no-op. */
+void lsp_plan_destroy(lsp_plan p);
+
+/*
+ * lsp_set_potential -- v(p_kappa) for kappa = 0..n-1 as n doubles, the diagonal
+ * of V_n (eq. Vn, Algorithm 1).  Copied into the plan.
+ * Errors: BAD_ARG (null), CUDA.
+ */
+int lsp_set_potential(lsp_plan p, const double* v, int on_device, void* stream);
+
+/*
+ * lsp_set_state -- initial samples u(p_kappa), n complex values.
+ *   u_prec  LSP_C64 (interleaved float pairs) or LSP_C128 (double pairs); it
+ *           need not match the plan precision (converted on the device).
+ * Errors: BAD_ARG, CUDA.
+ */
+int lsp_set_state(lsp_plan p, const void* u, int u_prec, int on_device, void* stream);
+
+/*
+ * lsp_strang_steps -- advance the state by nsteps Strang steps of size dt
+ * (eq. StrangTDSE; Algorithm 1 loop body in physical space):
+ *     u <- P o F^{-1} K F (P o u),  P = exp(-i dt v / (2 gamma)),
+ *     K_chi = exp(-i gamma 2 pi^2 ||h_chi||^2 dt)  (eq. Fourier-ODE, eq. Dn).
+ * Adjacent half potential steps are merged; the result is u at t + nsteps*dt.
+ * The phase tables are rebuilt on the device from v and ||h_chi||^2 with FP64
+ * argument reduction on every call.  nsteps = 0 is a no-op.
+ * Errors: BAD_ARG (nsteps < 0), CUDA, TIMEOUT (bounded grid barrier expired).
+ */
+int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream);
+
+/*
+ * lsp_get_state -- copy the state out.
+ *   out_prec  LSP_C64 or LSP_C128 element type of `out`.
+ *   space     LSP_SPACE_PHYSICAL: samples u(p_kappa), kappa order;
+ *             LSP_SPACE_SPECTRAL: coefficients uhat(h_chi), chi order (eq. approx_uhat).
+ * Host copies synchronise `stream` before returning.
+ * Errors: BAD_ARG, CUDA.
+ */
+int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device, void* stream);
+
+/* Lattice points p_kappa as n*d doubles (host), row-major (Def. 1). Errors: BAD_ARG, CUDA. */
+int lsp_lattice_points(lsp_plan p, double* x);
+
+/* ||h_chi||^2 for every bin chi, n int64 values (host) (eq. Dn / eq. hrepresenter). */
+int lsp_index_norms(lsp_plan p, int64_t* norms2);
+
+/*
+ * lsp_index_table -- one representative h_chi per bin, n*d int32 values (host),
+ * row-major.  MINL2 mode: a minimal-l2 vector of bin chi (eq. hrepresenter);
+ * when several exist, which one is returned is unspecified but fixed.
+ */
+int lsp_index_table(lsp_plan p, int32_t* h);
+
+/*
+ * lsp_plan_info -- plan geometry, 8 int64 values (host):
+ *   [0] n  [1] N1 (row length)  [2] N2 (column length)  [3] path (0 multipass,
+ *   1 SMEM-resident)  [4] precision  [5] device bytes held  [6] MINL2 DP box
+ *   half-width (0 for EXPLICIT)  [7] max ||h_chi||^2.
+ */
+int lsp_plan_info(lsp_plan p, int64_t* info);
+
+/*
+ * Batched stepping: many independent instances (same precision and device)
+ * advanced together by one persistent launch per call.
+ *   lsp_batch_create  plans: `count` plan handles (host array, borrowed: the
+ *                     plans must outlive the batch).  Errors: BAD_ARG, OOM, CUDA,
+ *                     UNSUPPORTED (mixed precision or device).
+ *   lsp_batch_steps   dt: `count` step sizes (host), one per instance;
+ *                     every instance advances nsteps steps.  Errors as
+ *                     lsp_strang_steps.
+ */
+int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count);
+int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream);
+void lsp_batch_destroy(lsp_batch b);
+
+/*
+ * lsp_adjoint -- gradient of a real objective J(u_T) of the final state with
+ * respect to the potential samples v and the initial state u_0, by the
+ * adjoint (conjugate-transposed) Strang step run backward: S^H = S(-dt),
+ * since every factor of eq. StrangTDSE is unitary.  Not in the paper.
+ *   dt, nsteps  as lsp_strang_steps; the plan's current state is u_0 and is
+ *               left at u_T = S^nsteps u_0 on return.
+ *   lamT        n complex (plan precision, device): dJ/dRe u_T + i dJ/dIm u_T.
+ *   grad_v      n doubles (device): receives dJ/dv_kappa.
+ *   grad_u0     n complex (plan precision, device): receives dJ/dRe u_0 + i dJ/dIm u_0.
+ *   ckpt_stride steps between stored forward checkpoints (0: ceil(sqrt(nsteps))).
+ * Errors: BAD_ARG, OOM, CUDA, TIMEOUT.
+ */
+int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double* grad_v,
+                void* grad_u0, int64_t ckpt_stride, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* lsp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSP_H */
