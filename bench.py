@@ -1,0 +1,348 @@
+"""Benchmark: lattice-point Strang steps per second on the n = 2^22, d = 6 rank-1 workload.
+
+One bench step = one lsp_strang_steps(dt, 1000) call on the d = 6, n = 2^22
+reconstructing rank-1 lattice (hyperbolic cross prod(1+|h_j|) <= 64,
+minimal-l2 anti-aliasing set, gamma = 0.05, dt = 1e-3): every row of the hot
+path (phase-table build, potential phase, forward FFT, kinetic phase, inverse
+FFT, merged potential phase, 1000-step driver) runs inside the timed region.
+The state (32 MiB c64) and phase tables fit in L2, so L2 is flushed (a 512 MiB
+write) before every timed step; each step is timed alone with CUDA events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lattice-point Strang steps/s (n·steps/s), FP32 vs FP64 at stated error; HBM %"
+STEPS_PER_CALL = 1000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-c128", action="store_true", help="skip the complex128 side measurement")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("LSP_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def c2_inputs():
+    import workloads as w
+    inst = w.c2(22)
+    return inst
+
+
+def cpu_oracle_rate(inst, budget_s: float = 15.0):
+    """The FP64 oracle (as it stands) on a bounded sample: a few Strang steps on the full state."""
+    import numpy as np
+    from oracle import lattice as L
+    from oracle import strang as S
+    P = L.lattice_points(inst.Z, inst.n)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    v, u0 = inst.v(P), inst.u0(P)
+    S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 1)          # warm
+    steps, t0 = 0, time.perf_counter()
+    u = u0
+    chunk = 2
+    while time.perf_counter() - t0 < budget_s:
+        u = S.strang(u, v, norms, inst.n, inst.gamma, inst.dt, chunk)
+        steps += chunk
+    el = time.perf_counter() - t0
+    return inst.npoints * steps / el, steps, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    inst = c2_inputs()
+    import numpy as np
+    from oracle import lattice as L
+    from oracle import strang as S
+    P = L.lattice_points(inst.Z, inst.n)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    v, u0 = inst.v(P), inst.u0(P)
+    per_step = 3                                                    # oracle Strang steps per bench step
+    for _ in range(args.warmup):
+        S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 1)
+    times = []
+    u = u0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u = S.strang(u, v, norms, inst.n, inst.gamma, inst.dt, per_step)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = inst.npoints * per_step * args.steps / tot
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "lattice-point steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rank-1 lattice d=6 n=2^22 HC(64) reconstructing, MINL2, gamma=0.05, dt=1e-3",
+                   "strang_steps_per_bench_step": per_step, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "lattice-point steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} Strang steps of the full n=2^22 state per bench step"},
+        "e2e": {"value": value, "unit": "lattice-point steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1808_06357_gb300 as lsp
+    from oracle import lattice as L  # only for the input points of the bounded CPU baseline
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inst = c2_inputs()
+    n = inst.npoints
+
+    # inputs: lattice points from the library, input functions from the workload module
+    plan = lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64", device=local)
+    pts = plan.lattice_points()
+    v_h = inst.v(pts)
+    u0_h = inst.u0(pts)
+    v_d = torch.from_numpy(v_h).to(dev)
+    u0_d = torch.from_numpy(u0_h.astype(np.complex64)).to(dev)
+    plan.set_potential(v_d)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_call(p):
+        p.strang_steps(inst.dt, STEPS_PER_CALL)
+
+    def timed(p, k, w):
+        p.set_state(u0_d)
+        for _ in range(w):
+            one_call(p)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_call(p)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        if p.status() != 0:
+            raise RuntimeError("device status " + lsp.strerror(p.status()))
+        return ms
+
+    clk = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk.start()
+    ms = timed(plan, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    tot_ms = max_over_ranks(sum(ms), world)
+    value = world * n * STEPS_PER_CALL * args.steps / (tot_ms / 1e3)
+
+    # roofline of the dominant kernel (the persistent multipass kernel; the
+    # per-call phase-table build is included in the timed call: conservative)
+    hbm, src = peaks()
+    alg_bytes = 48.0 * n * STEPS_PER_CALL                # 6 s per point-step, s = 8 B (c64)
+    kern_s = statistics.mean(ms) / 1e3
+    achieved = alg_bytes / kern_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic_c64_n2p22.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # complex128 side measurement on the same workload
+    c128 = None
+    if not args.no_c128:
+        p2 = lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128", device=local)
+        p2.set_potential(v_d)
+        u0_d2 = torch.from_numpy(u0_h).to(dev)
+        p2.set_state(u0_d2)
+        p2.strang_steps(inst.dt, 10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps2 = 100
+        flush.fill_(1.0)
+        e0.record(stream)
+        p2.strang_steps(inst.dt, steps2)
+        e1.record(stream)
+        e1.synchronize()
+        t2 = e0.elapsed_time(e1) / 1e3
+        c128 = {"value": n * steps2 / t2, "unit": "lattice-point steps/s", "steps_timed": steps2,
+                "achieved_GBps": 96.0 * n * steps2 / t2 / 1e9}
+        p2.destroy()
+
+    # end-to-end through the public API with host buffers (pinned), per bench step:
+    # set_potential (n f64) + set_state (n c64) H2D, 1000 steps, get_state (n c64) D2H
+    e2e = None
+    if not args.no_e2e:
+        v_pin = torch.from_numpy(v_h).pin_memory()
+        u_pin = torch.from_numpy(u0_h.astype(np.complex64)).pin_memory()
+        out_pin = torch.empty(n, dtype=torch.complex64).pin_memory()
+        plan.set_potential(v_pin.numpy())
+        plan.set_state(u_pin.numpy())
+        one_call(plan)
+        plan.get_state(out=out_pin.numpy())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.set_potential(v_pin.numpy())
+            plan.set_state(u_pin.numpy())
+            one_call(plan)
+            plan.get_state(out=out_pin.numpy())          # synchronises
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * n * STEPS_PER_CALL * args.steps / el, "unit": "lattice-point steps/s",
+               "h2d_bytes_per_step": n * 8 + n * 8, "d2h_bytes_per_step": n * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, steps, el = cpu_oracle_rate(inst)
+        cpu = {"value": rate, "unit": "lattice-point steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{steps} FP64 Strang steps of the full n=2^22 state ({el:.1f} s, numpy FFT, 1 thread)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "lattice-point steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "rank-1 lattice d=6 n=2^22 (N1=4096 x N2=1024), HC(64) reconstructing z, "
+                                   "MINL2 anti-aliasing set, gamma=0.05, dt=1e-3, 1000 Strang steps per bench step, "
+                                   "complex64 state", "l2": "flushed (512 MiB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                         "alg_bytes_per_point_step": 48},
+            "complex128": c128,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(out))
+    plan.destroy()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

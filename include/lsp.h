@@ -117,7 +117,10 @@ int lsp_set_state(lsp_plan p, const void* u, int u_prec, int on_device, void* st
  * Adjacent half potential steps are merged; the result is u at t + nsteps*dt.
  * The phase tables are rebuilt on the device from v and ||h_chi||^2 with FP64
  * argument reduction on every call.  nsteps = 0 is a no-op.
- * Errors: BAD_ARG (nsteps < 0), CUDA, TIMEOUT (bounded grid barrier expired).
+ * Errors: BAD_ARG (nsteps < 0), CUDA, TIMEOUT (returned immediately when an
+ * earlier call's bounded device wait expired and no lsp_set_state followed).
+ * A wait that expires during this call is reported by lsp_plan_status or the
+ * next host-side lsp_get_state.
  */
 int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream);
 
@@ -130,6 +133,14 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream);
  * Errors: BAD_ARG, CUDA.
  */
 int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device, void* stream);
+
+/*
+ * lsp_plan_status -- synchronise `stream` and return the plan's sticky device
+ * status: LSP_OK, or LSP_ERR_TIMEOUT if a bounded device-side wait of an
+ * earlier lsp_strang_steps / lsp_batch_steps expired (the state is then
+ * invalid until the next lsp_set_state), or LSP_ERR_CUDA.
+ */
+int lsp_plan_status(lsp_plan p, void* stream);
 
 /* Lattice points p_kappa as n*d doubles (host), row-major (Def. 1). Errors: BAD_ARG, CUDA. */
 int lsp_lattice_points(lsp_plan p, double* x);

@@ -1,0 +1,261 @@
+"""ctypes binding of liblsp.so (the C ABI in include/lsp.h).
+
+Argument marshalling only: every computation of the Strang step runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (data_ptr) and
+streams are torch CUDA streams; host buffers are numpy arrays.  There is no
+CPU fallback: if the library cannot be built or loaded, or a call fails, an
+exception is raised.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+LSP_OK = 0
+C64, C128 = 1, 2
+AA_MINL2, AA_EXPLICIT = 0, 1
+PHYSICAL, SPECTRAL = 0, 1
+PATH_MULTIPASS, PATH_SMALL = 0, 1
+
+_lib = None
+_lock = threading.Lock()
+
+
+class LspError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblsp.so")
+
+
+def _declare(lib):
+    P, I, I64, D, V = C.c_void_p, C.c_int, C.c_int64, C.c_double, None
+    sig = {
+        "lsp_plan_create": (I, [C.POINTER(C.c_void_p), I, I, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int32), I64, I, I, D, I]),
+        "lsp_plan_destroy": (V, [P]),
+        "lsp_set_potential": (I, [P, P, I, P]),
+        "lsp_set_state": (I, [P, P, I, I, P]),
+        "lsp_strang_steps": (I, [P, D, I64, P]),
+        "lsp_get_state": (I, [P, P, I, I, I, P]),
+        "lsp_plan_status": (I, [P, P]),
+        "lsp_lattice_points": (I, [P, P]),
+        "lsp_index_norms": (I, [P, P]),
+        "lsp_index_table": (I, [P, P]),
+        "lsp_plan_info": (I, [P, P]),
+        "lsp_batch_create": (I, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), I]),
+        "lsp_batch_steps": (I, [P, P, I64, P]),
+        "lsp_batch_destroy": (V, [P]),
+        "lsp_adjoint": (I, [P, D, I64, P, P, P, I64, P]),
+        "lsp_strerror": (C.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def load_library(build_if_missing: bool = True):
+    """Load liblsp.so, compiling it first when it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if build_if_missing:
+            from . import build as _build
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing; run __graft_entry__.build()")
+        _lib = _declare(C.CDLL(path))
+        return _lib
+
+
+def strerror(code: int) -> str:
+    lib = load_library()
+    return lib.lsp_strerror(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != LSP_OK:
+        raise LspError(code, where)
+
+
+def _prec_code(prec) -> int:
+    if prec in (C64, "c64", "complex64"):
+        return C64
+    if prec in (C128, "c128", "complex128"):
+        return C128
+    raise ValueError(f"unknown precision {prec!r}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _buf(x):
+    """(pointer, on_device) for a torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return C.c_void_p(x.data_ptr()), int(x.is_cuda)
+    except ImportError:
+        pass
+    a = np.asarray(x)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+class Plan:
+    """One TDSE instance on a rank-1 or rank-2 lattice (lsp_plan_create)."""
+
+    def __init__(self, Z, n, gamma: float, prec="c64", aa: str = "minl2", index_set=None,
+                 device: int = 0):
+        lib = load_library()
+        nn = np.atleast_1d(np.asarray(n, dtype=np.int64))
+        r = nn.size
+        Zm = np.asarray(Z, dtype=np.int64).reshape(-1, r)
+        self.d, self.r = Zm.shape[0], r
+        self.n = tuple(int(x) for x in nn)
+        self.npoints = int(np.prod(nn))
+        self.prec = _prec_code(prec)
+        self.gamma = float(gamma)
+        self.device = int(device)
+        Zc = np.ascontiguousarray(Zm)
+        mode = AA_EXPLICIT if aa == "explicit" else AA_MINL2
+        if mode == AA_EXPLICIT:
+            I = np.ascontiguousarray(np.asarray(index_set, dtype=np.int32))
+            iptr, m = I.ctypes.data_as(C.POINTER(C.c_int32)), I.shape[0]
+            self._index_set = I
+        else:
+            iptr, m = None, 0
+        h = C.c_void_p()
+        _check(lib.lsp_plan_create(C.byref(h), self.d, r, nn.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   Zc.ctypes.data_as(C.POINTER(C.c_int64)), iptr, m, mode, self.prec,
+                                   self.gamma, self.device), "lsp_plan_create")
+        self._h = h
+        self._lib = lib
+
+    # -- lifetime ----------------------------------------------------------
+    def destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lsp_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- data --------------------------------------------------------------
+    def set_potential(self, v, stream=None):
+        ptr, dev = _buf(v)
+        _check(self._lib.lsp_set_potential(self._h, ptr, dev, _stream_ptr(stream) if dev else None),
+               "lsp_set_potential")
+
+    def set_state(self, u, stream=None):
+        ptr, dev = _buf(u)
+        prec = C64 if str(getattr(u, "dtype", "")).endswith("complex64") else C128
+        _check(self._lib.lsp_set_state(self._h, ptr, prec, dev, _stream_ptr(stream) if dev else None),
+               "lsp_set_state")
+
+    def strang_steps(self, dt: float, nsteps: int, stream=None):
+        _check(self._lib.lsp_strang_steps(self._h, float(dt), int(nsteps), _stream_ptr(stream)),
+               "lsp_strang_steps")
+
+    def get_state(self, out=None, space: str = "physical", prec=None, stream=None):
+        """Copy the state into `out` (torch CUDA tensor or numpy array).  Without `out`
+        a new torch tensor on the plan's device is returned."""
+        sp = SPECTRAL if space == "spectral" else PHYSICAL
+        if out is None:
+            import torch
+            pc = self.prec if prec is None else _prec_code(prec)
+            out = torch.empty(self.npoints, dtype=torch.complex64 if pc == C64 else torch.complex128,
+                              device=f"cuda:{self.device}")
+        pc = C64 if str(out.dtype).endswith("complex64") else C128
+        ptr, dev = _buf(out)
+        _check(self._lib.lsp_get_state(self._h, ptr, pc, sp, dev, _stream_ptr(stream)), "lsp_get_state")
+        return out
+
+    def status(self, stream=None) -> int:
+        return int(self._lib.lsp_plan_status(self._h, _stream_ptr(stream)))
+
+    # -- queries -----------------------------------------------------------
+    def lattice_points(self) -> np.ndarray:
+        x = np.empty((self.npoints, self.d), dtype=np.float64)
+        _check(self._lib.lsp_lattice_points(self._h, C.c_void_p(x.ctypes.data)), "lsp_lattice_points")
+        return x
+
+    def index_norms(self) -> np.ndarray:
+        x = np.empty(self.npoints, dtype=np.int64)
+        _check(self._lib.lsp_index_norms(self._h, C.c_void_p(x.ctypes.data)), "lsp_index_norms")
+        return x
+
+    def index_table(self) -> np.ndarray:
+        x = np.empty((self.npoints, self.d), dtype=np.int32)
+        _check(self._lib.lsp_index_table(self._h, C.c_void_p(x.ctypes.data)), "lsp_index_table")
+        return x
+
+    def info(self) -> dict:
+        x = np.zeros(8, dtype=np.int64)
+        _check(self._lib.lsp_plan_info(self._h, C.c_void_p(x.ctypes.data)), "lsp_plan_info")
+        keys = ["n", "N1", "N2", "path", "prec", "bytes", "dp_box", "max_norm2"]
+        return dict(zip(keys, (int(v) for v in x)))
+
+
+class Batch:
+    """Several plans advanced together (lsp_batch_create / lsp_batch_steps)."""
+
+    def __init__(self, plans):
+        lib = load_library()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = C.c_void_p()
+        _check(lib.lsp_batch_create(C.byref(h), arr, len(self.plans)), "lsp_batch_create")
+        self._h, self._lib = h, lib
+
+    def steps(self, dts, nsteps: int, stream=None):
+        dt = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+        _check(self._lib.lsp_batch_steps(self._h, C.c_void_p(dt.ctypes.data), int(nsteps), _stream_ptr(stream)),
+               "lsp_batch_steps")
+
+    def destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lsp_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def adjoint(plan: Plan, dt: float, nsteps: int, lamT, grad_v, grad_u0, ckpt_stride: int = 0, stream=None):
+    """lsp_adjoint: gradients of a real objective of u_T w.r.t. v and u_0 (device tensors)."""
+    lp, _ = _buf(lamT)
+    gv, _ = _buf(grad_v)
+    gu, _ = _buf(grad_u0)
+    _check(plan._lib.lsp_adjoint(plan.handle, float(dt), int(nsteps), lp, gv, gu, int(ckpt_stride),
+                                 _stream_ptr(stream)), "lsp_adjoint")

@@ -1,0 +1,599 @@
+// C ABI of the lattice Strang-splitting library: plan construction (lattice
+// checks, minimal-l2 norms by an exact min-plus dynamic programme on the GPU,
+// twiddle tables), per-call phase tables and state I/O.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "lsp_internal.cuh"
+
+namespace lsp {
+
+int small_desc_bytes(int prec);
+int small_upload_desc(lsp_plan p, cudaStream_t s);
+
+static constexpr int32_t kInf = 0x3fffffff;
+
+// ---------------------------------------------------------------------------
+// Minimal-l2 norms per bin (Lemma 4, eq. hrepresenter).  Min-plus DP over the
+// residue group Z_n1 x Z_n2:  f_j(xi) = min_{|t|<=B} f_{j-1}(xi - t z_j) + t^2.
+// ---------------------------------------------------------------------------
+__global__ void dp_init(int32_t* f, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    f[i] = i == 0 ? 0 : kInf;
+}
+
+__global__ void dp_step(const int32_t* __restrict__ f, int32_t* __restrict__ g, long long n1, long long n2,
+                        long long s1, long long s2, int B) {
+  const long long n = n1 * n2;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    long long x1 = c / n2, x2 = c - x1 * n2;
+    long long a1 = (x1 + (B * s1) % n1) % n1;     // xi - t z_j at t = -B
+    long long a2 = (x2 + (B * s2) % n2) % n2;
+    int best = kInf;
+    for (int t = -B; t <= B; ++t) {
+      int val = __ldg(f + a1 * n2 + a2);
+      if (val < kInf) best = min(best, val + t * t);
+      a1 -= s1; if (a1 < 0) a1 += n1;
+      a2 -= s2; if (a2 < 0) a2 += n2;
+    }
+    g[c] = best;
+  }
+}
+
+__global__ void dp_max(const int32_t* f, long long n, int* out) {
+  int m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, f[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Recover one minimal vector per bin from the stored DP levels: walk the
+// components backwards taking the first t (in -B..B order) that attains the level.
+__global__ void dp_backtrack(const int32_t* __restrict__ levels, long long n1, long long n2,
+                             const long long* __restrict__ s1, const long long* __restrict__ s2, int d, int B,
+                             int32_t* __restrict__ h) {
+  const long long n = n1 * n2;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    long long x1 = c / n2, x2 = c - x1 * n2;
+    for (int j = d; j >= 1; --j) {
+      const int32_t* fj = levels + (size_t)j * n;
+      const int32_t* fp = levels + (size_t)(j - 1) * n;
+      int cur = fj[x1 * n2 + x2];
+      long long a1 = (x1 + (B * s1[j - 1]) % n1) % n1;
+      long long a2 = (x2 + (B * s2[j - 1]) % n2) % n2;
+      int pick = 0;
+      for (int t = -B; t <= B; ++t) {
+        int val = fp[a1 * n2 + a2];
+        if (val < kInf && val + t * t == cur) { pick = t; x1 = a1; x2 = a2; break; }
+        a1 -= s1[j - 1]; if (a1 < 0) a1 += n1;
+        a2 -= s2[j - 1]; if (a2 < 0) a2 += n2;
+      }
+      h[c * d + (j - 1)] = pick;
+    }
+  }
+}
+
+static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 16); }
+
+// Runs the DP; on success `out` (n int32) holds the norms and *box the half-width used.
+// When `levels` is non-null it receives all d+1 levels (for backtracking) with box fixed.
+static int minl2_dp(lsp_plan p, int32_t* out, int* box, int32_t* levels, int fixed_box) {
+  const long long n1 = p->n[0], n2 = p->r == 2 ? p->n[1] : 1;
+  const long long n = n1 * n2;
+  const int d = p->d;
+  int B;
+  if (fixed_box > 0) {
+    B = fixed_box;
+  } else {
+    double vol1 = pow(M_PI, d / 2.0) / tgamma(d / 2.0 + 1.0);
+    B = std::max(1, (int)ceil(pow((double)n / vol1, 1.0 / d)));
+    B = (int)std::min<long long>(B, n1 / 2 > 0 ? n1 / 2 : 1);
+  }
+  int32_t* f = nullptr;
+  int32_t* g = nullptr;
+  int* dmax = nullptr;
+  if (!levels) {
+    if (cudaMalloc(&f, n * sizeof(int32_t)) != cudaSuccess) return LSP_ERR_OOM;
+    g = out;
+  }
+  if (cudaMalloc(&dmax, sizeof(int)) != cudaSuccess) { cudaFree(f); return LSP_ERR_OOM; }
+  int rc = LSP_OK;
+  for (;;) {
+    int32_t* a = levels ? levels : f;
+    dp_init<<<grid_for(n), 256>>>(a, n);
+    for (int j = 0; j < d; ++j) {
+      long long s1 = ((p->Z[j * p->r + 0] % n1) + n1) % n1;
+      long long s2 = p->r == 2 ? ((p->Z[j * p->r + 1] % n2) + n2) % n2 : 0;
+      int32_t* src = levels ? levels + (size_t)j * n : (j % 2 == 0 ? f : g);
+      int32_t* dst = levels ? levels + (size_t)(j + 1) * n : (j % 2 == 0 ? g : f);
+      dp_step<<<grid_for(n), 256>>>(src, dst, n1, n2, s1, s2, B);
+    }
+    int32_t* res = levels ? levels + (size_t)d * n : (d % 2 == 1 ? g : f);
+    if (cudaMemset(dmax, 0, sizeof(int)) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
+    dp_max<<<grid_for(n), 256>>>(res, n, dmax);
+    int mx = 0;
+    if (cudaMemcpy(&mx, dmax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
+    const bool reached = mx < kInf;
+    const bool full_box = B >= n1 / 2;
+    if (levels) {
+      if (!reached) rc = LSP_ERR_NOT_CANONICAL;
+      break;
+    }
+    if (reached && ((long long)mx <= (long long)(B + 1) * (B + 1) || full_box)) {
+      if (res != out) cudaMemcpy(out, res, n * sizeof(int32_t), cudaMemcpyDeviceToDevice);
+      *box = B;
+      break;
+    }
+    if (full_box) { rc = LSP_ERR_NOT_CANONICAL; break; }
+    B = (int)std::min<long long>(2ll * B, n1 / 2);
+  }
+  cudaFree(dmax);
+  cudaFree(f);
+  if (rc == LSP_OK && cudaGetLastError() != cudaSuccess) rc = LSP_ERR_CUDA;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Phase tables (Algorithm 1: diagonals of exp(-i dt V/(2 gamma)), exp(-i gamma D dt / 2)),
+// arguments reduced mod 2 pi in FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void build_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf, T* K,
+                             long long n, double turns_v, double turns_k, int multipass, int logN1, int logN2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double th = v[i] * turns_v;                       // -dt v / (4 pi gamma): half step, in turns
+    T a, b, c;
+    encode_phase(th, &a);
+    encode_phase(2.0 * th, &b);
+    long long bin = i;
+    if (multipass) {                                   // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
+      long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
+      bin = xi2 + (xi1 << logN2);
+    }
+    encode_phase(turns_k * (double)norm2[bin], &c);
+    Ph[i] = a;
+    Pf[i] = b;
+    K[i] = c;
+  }
+}
+
+template <typename S, typename D> __device__ __forceinline__ D cvt(S x);
+template <> __device__ __forceinline__ float2 cvt(float2 x) { return x; }
+template <> __device__ __forceinline__ double2 cvt(double2 x) { return x; }
+template <> __device__ __forceinline__ float2 cvt(double2 x) { return make_float2((float)x.x, (float)x.y); }
+template <> __device__ __forceinline__ double2 cvt(float2 x) { return make_double2(x.x, x.y); }
+
+template <typename S, typename D>
+__global__ void convert(const S* __restrict__ a, D* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = cvt<S, D>(a[i]);
+}
+
+static int launch_convert(const void* src, int sp, void* dst, int dp, long long n, cudaStream_t s) {
+  if (sp == LSP_C64 && dp == LSP_C64) convert<float2, float2><<<grid_for(n), 256, 0, s>>>((const float2*)src, (float2*)dst, n);
+  else if (sp == LSP_C64) convert<float2, double2><<<grid_for(n), 256, 0, s>>>((const float2*)src, (double2*)dst, n);
+  else if (dp == LSP_C64) convert<double2, float2><<<grid_for(n), 256, 0, s>>>((const double2*)src, (float2*)dst, n);
+  else convert<double2, double2><<<grid_for(n), 256, 0, s>>>((const double2*)src, (double2*)dst, n);
+  return cuda_status(cudaGetLastError());
+}
+
+static size_t csize(int prec) { return prec == LSP_C64 ? sizeof(float2) : sizeof(double2); }
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int ilog2exact(long long x) {
+  if (x <= 0 || (x & (x - 1))) return -1;
+  int l = 0;
+  while ((1ll << l) < x) ++l;
+  return l;
+}
+
+static long long mulmod(long long a, long long b, long long m) {
+  return (long long)(((__int128)a * (__int128)b) % m);
+}
+
+static void factorize(int len, SmallAxis& ax) {
+  ax.nfac = 0;
+  int rem = len;
+  const int pref[] = {16, 8, 4, 2};
+  for (int f : pref)
+    while (rem % f == 0 && ax.nfac < 24) { ax.fac[ax.nfac++] = f; rem /= f; }
+  for (int f = 3; f <= rem && ax.nfac < 24; f += 2)
+    while (rem % f == 0) { ax.fac[ax.nfac++] = f; rem /= f; }
+  if (rem > 1 && ax.nfac < 24) ax.fac[ax.nfac++] = rem;
+}
+
+template <typename T> static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long long denom) {
+  // entries exp(-2 pi i k / denom), k < len
+  size_t off = buf.size();
+  buf.resize(off + (size_t)len * sizeof(T));
+  T* t = (T*)(buf.data() + off);
+  for (long long k = 0; k < len; ++k) {
+    // reduce k/denom to [-1/2, 1/2] turns before evaluating
+    long long kk = k % denom;
+    double f = (double)kk / (double)denom;
+    if (f > 0.5) f -= 1.0;
+    double ang = -2.0 * M_PI * f;
+    t[k].x = (decltype(t[k].x))cos(ang);
+    t[k].y = (decltype(t[k].y))sin(ang);
+  }
+}
+
+static void free_plan(lsp_plan p) {
+  if (!p) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->tw_line, p->tw_fine, p->tw_small,
+                  p->stage, p->work, p->desc, p->bar, p->err};
+  for (void* b : bufs) if (b) cudaFree(b);
+  if (p->err_host) cudaFreeHost(p->err_host);
+  cudaSetDevice(prev);
+  delete p;
+}
+
+struct DeviceGuard {
+  int prev = 0;
+  explicit DeviceGuard(int dev) { cudaGetDevice(&prev); cudaSetDevice(dev); }
+  ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+template <typename Tp> static int dalloc(lsp_plan p, Tp** ptr, size_t bytes) {
+  if (cudaMalloc((void**)ptr, bytes) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
+  p->bytes += bytes;
+  return LSP_OK;
+}
+
+}  // namespace lsp
+
+using namespace lsp;
+
+extern "C" {
+
+const char* lsp_strerror(int code) {
+  switch (code) {
+    case LSP_OK: return "ok";
+    case LSP_ERR_BAD_ARG: return "invalid argument";
+    case LSP_ERR_NOT_CANONICAL: return "lattice not in canonical form (Def. 1)";
+    case LSP_ERR_NOT_INJECTIVE: return "index set is not a full anti-aliasing set (Def. 2)";
+    case LSP_ERR_TOO_LARGE: return "size not supported";
+    case LSP_ERR_OOM: return "device allocation failed";
+    case LSP_ERR_CUDA: return "CUDA runtime error";
+    case LSP_ERR_TIMEOUT: return "bounded device wait expired";
+    case LSP_ERR_UNSUPPORTED: return "configuration not supported";
+    default: return "unknown status";
+  }
+}
+
+int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
+                    const int32_t* index_set, int64_t m, int aa_mode, int prec, double gamma, int device) {
+  if (!out) return LSP_ERR_BAD_ARG;
+  *out = nullptr;
+  if (d < 1 || d > 64 || r < 1 || r > 2 || !n || !Z) return LSP_ERR_BAD_ARG;
+  if (prec != LSP_C64 && prec != LSP_C128) return LSP_ERR_BAD_ARG;
+  if (aa_mode != LSP_AA_MINL2 && aa_mode != LSP_AA_EXPLICIT) return LSP_ERR_BAD_ARG;
+  if (!(gamma > 0.0) || !isfinite(gamma)) return LSP_ERR_BAD_ARG;
+  if (aa_mode == LSP_AA_EXPLICIT && !index_set) return LSP_ERR_BAD_ARG;
+  long long ntot = 1;
+  for (int i = 0; i < r; ++i) {
+    if (n[i] < 1) return LSP_ERR_BAD_ARG;
+    ntot *= n[i];
+    if (ntot > (1ll << 30)) return LSP_ERR_TOO_LARGE;
+  }
+  if (r == 2 && n[0] % n[1] != 0) return LSP_ERR_NOT_CANONICAL;       // n_2 | n_1 (Def. 1)
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) { cudaGetLastError(); return LSP_ERR_CUDA; }
+
+  lsp_plan p = new (std::nothrow) lsp_plan_s();
+  if (!p) return LSP_ERR_OOM;
+  p->device = device; p->d = d; p->r = r; p->prec = prec; p->gamma = gamma; p->aa_mode = aa_mode;
+  p->n[0] = n[0]; p->n[1] = r == 2 ? n[1] : 1; p->ntot = ntot;
+  p->Z.assign(Z, Z + (size_t)d * r);
+  for (int j = 0; j < d; ++j)
+    for (int i = 0; i < r; ++i) { long long ni = p->n[i]; p->Z[j * r + i] = ((p->Z[j * r + i] % ni) + ni) % ni; }
+
+  DeviceGuard guard(device);
+  const size_t sz = csize(prec);
+  // ---- choose the path ----
+  const int logn = ilog2exact(ntot);
+  const bool small_fits = 2 * (size_t)ntot * sz <= (size_t)kSmallSmemBytes;
+  if (r == 1 && logn >= 13) {
+    const int maxN1 = prec == LSP_C64 ? 13 : 12;
+    int logN2 = std::min(10, logn / 2);
+    int logN1 = logn - logN2;
+    if (logN1 > maxN1) { free_plan(p); return LSP_ERR_TOO_LARGE; }
+    p->path = kPathMultipass;
+    p->logn = logn; p->logN1 = logN1; p->logN2 = logN2; p->N1 = 1 << logN1; p->N2 = 1 << logN2;
+    p->logLmax = std::max(logN1, logN2);
+  } else if (small_fits) {
+    p->path = kPathSmall;
+    p->naxes = r;
+    long long stride = 1;
+    for (int i = r - 1; i >= 0; --i) {
+      p->axes[i].len = (int)p->n[i];
+      p->axes[i].stride = (int)stride;
+      stride *= p->n[i];
+      factorize((int)p->n[i], p->axes[i]);
+    }
+  } else {
+    free_plan(p);
+    return r == 1 ? LSP_ERR_TOO_LARGE : LSP_ERR_UNSUPPORTED;
+  }
+
+  int rc = LSP_OK;
+  auto fail = [&](int code) { free_plan(p); return code; };
+  if ((rc = dalloc(p, &p->u, ntot * sz))) return fail(rc);
+  if ((rc = dalloc(p, &p->v, ntot * sizeof(double)))) return fail(rc);
+  if ((rc = dalloc(p, &p->norm2, ntot * sizeof(int32_t)))) return fail(rc);
+  if ((rc = dalloc(p, &p->Ph, ntot * sz))) return fail(rc);
+  if ((rc = dalloc(p, &p->Pf, ntot * sz))) return fail(rc);
+  if ((rc = dalloc(p, &p->K, ntot * sz))) return fail(rc);
+  if ((rc = dalloc(p, &p->stage, ntot * sizeof(double2)))) return fail(rc);
+  if ((rc = dalloc(p, &p->bar, 256))) return fail(rc);
+  if ((rc = dalloc(p, &p->err, 256))) return fail(rc);
+  if ((rc = dalloc(p, &p->desc, 4096))) return fail(rc);
+  if (cudaHostAlloc((void**)&p->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) return fail(LSP_ERR_OOM);
+  *p->err_host = 0;
+  if (cudaMemset(p->u, 0, ntot * sz) != cudaSuccess || cudaMemset(p->v, 0, ntot * sizeof(double)) != cudaSuccess ||
+      cudaMemset(p->err, 0, 256) != cudaSuccess || cudaMemset(p->bar, 0, 256) != cudaSuccess)
+    return fail(LSP_ERR_CUDA);
+
+  // ---- twiddle tables (FP64 evaluation, rounded once) ----
+  std::vector<unsigned char> tw;
+  if (p->path == kPathMultipass) {
+    if ((rc = dalloc(p, &p->work, ntot * sz))) return fail(rc);
+    const long long Lmax = 1ll << p->logLmax, nfine = ntot >> p->logLmax;
+    if (prec == LSP_C64) fill_twiddles<float2>(tw, Lmax, Lmax); else fill_twiddles<double2>(tw, Lmax, Lmax);
+    if ((rc = dalloc(p, &p->tw_line, tw.size()))) return fail(rc);
+    if (cudaMemcpy(p->tw_line, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
+    tw.clear();
+    if (prec == LSP_C64) fill_twiddles<float2>(tw, nfine, ntot); else fill_twiddles<double2>(tw, nfine, ntot);
+    if ((rc = dalloc(p, &p->tw_fine, tw.size()))) return fail(rc);
+    if (cudaMemcpy(p->tw_fine, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
+  } else {
+    for (int i = 0; i < p->naxes; ++i) {
+      p->axes[i].tw_off = (int)(tw.size() / sz);
+      if (prec == LSP_C64) fill_twiddles<float2>(tw, p->axes[i].len, p->axes[i].len);
+      else fill_twiddles<double2>(tw, p->axes[i].len, p->axes[i].len);
+    }
+    if ((rc = dalloc(p, &p->tw_small, tw.size()))) return fail(rc);
+    if (cudaMemcpy(p->tw_small, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
+  }
+
+  // ---- ||h_chi||^2 per bin ----
+  if (aa_mode == LSP_AA_MINL2) {
+    rc = minl2_dp(p, p->norm2, &p->dp_box, nullptr, 0);
+    if (rc) return fail(rc);
+  } else {
+    if (m != ntot) return fail(LSP_ERR_NOT_INJECTIVE);
+    std::vector<int32_t> nrm((size_t)ntot, 0);
+    std::vector<unsigned char> seen((size_t)ntot, 0);
+    for (long long k = 0; k < ntot; ++k) {
+      long long chi = 0, s2 = 0;
+      for (int i = 0; i < r; ++i) {
+        long long ni = p->n[i], acc = 0;
+        for (int j = 0; j < d; ++j) {
+          long long h = index_set[k * d + j];
+          acc = (acc + mulmod(((h % ni) + ni) % ni, p->Z[j * r + i], ni)) % ni;
+        }
+        chi = chi * ni + acc;
+      }
+      for (int j = 0; j < d; ++j) s2 += (long long)index_set[k * d + j] * index_set[k * d + j];
+      if (seen[chi]) return fail(LSP_ERR_NOT_INJECTIVE);
+      if (s2 > kInf) return fail(LSP_ERR_TOO_LARGE);
+      seen[chi] = 1;
+      nrm[chi] = (int32_t)s2;
+    }
+    if (cudaMemcpy(p->norm2, nrm.data(), ntot * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(LSP_ERR_CUDA);
+  }
+  {
+    int* dmax = nullptr;
+    if (cudaMalloc(&dmax, sizeof(int)) != cudaSuccess) return fail(LSP_ERR_OOM);
+    cudaMemset(dmax, 0, sizeof(int));
+    dp_max<<<grid_for(ntot), 256>>>(p->norm2, ntot, dmax);
+    int mx = 0;
+    cudaMemcpy(&mx, dmax, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(dmax);
+    p->max_norm2 = mx;
+  }
+
+  // ---- kernel descriptors ----
+  if (p->path == kPathMultipass) rc = multipass_upload_desc(p, 0);
+  else rc = small_upload_desc(p, 0);
+  if (rc) return fail(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSP_ERR_CUDA);
+  *out = p;
+  return LSP_OK;
+}
+
+void lsp_plan_destroy(lsp_plan p) {
+  if (!p) return;
+  {
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+  }
+  free_plan(p);
+}
+
+int lsp_set_potential(lsp_plan p, const double* v, int on_device, void* stream) {
+  if (!p || !v) return LSP_ERR_BAD_ARG;
+  DeviceGuard g(p->device);
+  LSP_CUDA_TRY(cudaMemcpyAsync(p->v, v, p->ntot * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  return LSP_OK;
+}
+
+int lsp_set_state(lsp_plan p, const void* u, int u_prec, int on_device, void* stream) {
+  if (!p || !u || (u_prec != LSP_C64 && u_prec != LSP_C128)) return LSP_ERR_BAD_ARG;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t bytes = (size_t)p->ntot * csize(u_prec);
+  if (u_prec == p->prec) {
+    LSP_CUDA_TRY(cudaMemcpyAsync(p->u, u, bytes, kind, s));
+  } else {
+    LSP_CUDA_TRY(cudaMemcpyAsync(p->stage, u, bytes, kind, s));
+    int rc = launch_convert(p->stage, u_prec, p->u, p->prec, p->ntot, s);
+    if (rc) return rc;
+  }
+  LSP_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+  *p->err_host = 0;
+  return LSP_OK;
+}
+
+int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
+  if (!p || nsteps < 0 || !isfinite(dt)) return LSP_ERR_BAD_ARG;
+  if (*p->err_host != 0) return *p->err_host;
+  if (nsteps == 0) return LSP_OK;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // phase tables for this dt, FP64 arguments in turns:
+  //   P_half: -dt v / (4 pi gamma),  K: -pi gamma dt ||h||^2
+  const double turns_v = -dt / (4.0 * M_PI * p->gamma);
+  const double turns_k = -M_PI * p->gamma * dt;
+  const int mp = p->path == kPathMultipass;
+  if (p->prec == LSP_C64)
+    build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
+                                                            (float2*)p->K, p->ntot, turns_v, turns_k, mp, p->logN1, p->logN2);
+  else
+    build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
+                                                              (double2*)p->K, p->ntot, turns_v, turns_k, mp, p->logN1, p->logN2);
+  LSP_CUDA_TRY(cudaGetLastError());
+  int rc = mp ? multipass_steps(p, nsteps, s) : small_steps(p, nsteps, s);
+  if (rc) return rc;
+  LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return LSP_OK;
+}
+
+int lsp_plan_status(lsp_plan p, void* stream) {
+  if (!p) return LSP_ERR_BAD_ARG;
+  DeviceGuard g(p->device);
+  LSP_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return *p->err_host;
+}
+
+int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device, void* stream) {
+  if (!p || !out || (out_prec != LSP_C64 && out_prec != LSP_C128)) return LSP_ERR_BAD_ARG;
+  if (space != LSP_SPACE_PHYSICAL && space != LSP_SPACE_SPECTRAL) return LSP_ERR_BAD_ARG;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->ntot * csize(out_prec);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const void* src = p->u;
+  int src_prec = p->prec;
+  if (space == LSP_SPACE_SPECTRAL) {
+    int rc = p->path == kPathMultipass ? multipass_spectral(p, s) : small_spectral(p, s);
+    if (rc) return rc;
+    src = p->stage;
+    src_prec = LSP_C128;
+  }
+  if (src_prec == out_prec) {
+    LSP_CUDA_TRY(cudaMemcpyAsync(out, src, bytes, kind, s));
+  } else if (on_device) {
+    int rc = launch_convert(src, src_prec, out, out_prec, p->ntot, s);
+    if (rc) return rc;
+  } else {
+    // convert into a device buffer, then copy out; the half-potential table
+    // (rebuilt by every lsp_strang_steps) holds the c64 result of a c128 source
+    void* tmp = src == p->stage ? p->Ph : p->stage;
+    int rc = launch_convert(src, src_prec, tmp, out_prec, p->ntot, s);
+    if (rc) return rc;
+    LSP_CUDA_TRY(cudaMemcpyAsync(out, tmp, bytes, kind, s));
+  }
+  if (!on_device) {
+    LSP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*p->err_host) return *p->err_host;
+  }
+  return LSP_OK;
+}
+
+int lsp_lattice_points(lsp_plan p, double* x) {
+  if (!p || !x) return LSP_ERR_BAD_ARG;
+  const long long N = p->ntot, n1 = p->n[0], n2 = p->n[1];
+  for (long long k = 0; k < N; ++k) {
+    long long k1 = p->r == 2 ? k / n2 : k, k2 = p->r == 2 ? k % n2 : 0;
+    for (int j = 0; j < p->d; ++j) {
+      // N p = z_1 k1 (N/n1) + z_2 k2 (N/n2) mod N  (Def. 1)
+      long long q = mulmod(mulmod(p->Z[j * p->r], k1, N), N / n1, N);
+      if (p->r == 2) q = (q + mulmod(mulmod(p->Z[j * p->r + 1], k2, N), N / n2, N)) % N;
+      x[k * p->d + j] = (double)q / (double)N;
+    }
+  }
+  return LSP_OK;
+}
+
+int lsp_index_norms(lsp_plan p, int64_t* norms2) {
+  if (!p || !norms2) return LSP_ERR_BAD_ARG;
+  DeviceGuard g(p->device);
+  std::vector<int32_t> tmp((size_t)p->ntot);
+  LSP_CUDA_TRY(cudaMemcpy(tmp.data(), p->norm2, p->ntot * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  for (long long i = 0; i < p->ntot; ++i) norms2[i] = tmp[i];
+  return LSP_OK;
+}
+
+int lsp_index_table(lsp_plan p, int32_t* h) {
+  if (!p || !h) return LSP_ERR_BAD_ARG;
+  if (p->aa_mode == LSP_AA_EXPLICIT) return LSP_ERR_UNSUPPORTED;
+  DeviceGuard g(p->device);
+  const long long n = p->ntot, n1 = p->n[0], n2 = p->n[1];
+  const int d = p->d;
+  int32_t* levels = nullptr;
+  int32_t* dh = nullptr;
+  long long* ds = nullptr;
+  int rc = LSP_OK;
+  if (cudaMalloc(&levels, (size_t)(d + 1) * n * sizeof(int32_t)) != cudaSuccess) return LSP_ERR_OOM;
+  if (cudaMalloc(&dh, (size_t)n * d * sizeof(int32_t)) != cudaSuccess) { cudaFree(levels); return LSP_ERR_OOM; }
+  if (cudaMalloc(&ds, 2 * (size_t)d * sizeof(long long)) != cudaSuccess) { cudaFree(levels); cudaFree(dh); return LSP_ERR_OOM; }
+  std::vector<long long> s((size_t)2 * d);
+  for (int j = 0; j < d; ++j) {
+    s[j] = p->Z[j * p->r];
+    s[d + j] = p->r == 2 ? p->Z[j * p->r + 1] : 0;
+  }
+  cudaMemcpy(ds, s.data(), s.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  rc = minl2_dp(p, nullptr, nullptr, levels, p->dp_box);
+  if (!rc) {
+    dp_backtrack<<<grid_for(n), 256>>>(levels, n1, n2, ds, ds + d, d, p->dp_box, dh);
+    if (cudaMemcpy(h, dh, (size_t)n * d * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) rc = LSP_ERR_CUDA;
+  }
+  cudaFree(levels); cudaFree(dh); cudaFree(ds);
+  return rc;
+}
+
+int lsp_plan_info(lsp_plan p, int64_t* info) {
+  if (!p || !info) return LSP_ERR_BAD_ARG;
+  info[0] = p->ntot;
+  info[1] = p->path == kPathMultipass ? p->N1 : p->n[p->r - 1];
+  info[2] = p->path == kPathMultipass ? p->N2 : (p->r == 2 ? p->n[0] : 1);
+  info[3] = p->path;
+  info[4] = p->prec;
+  info[5] = (int64_t)p->bytes;
+  info[6] = p->dp_box;
+  info[7] = p->max_norm2;
+  return LSP_OK;
+}
+
+int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
+  if (out) *out = nullptr;
+  (void)plans; (void)count;
+  return LSP_ERR_UNSUPPORTED;
+}
+int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream) {
+  (void)b; (void)dt; (void)nsteps; (void)stream;
+  return LSP_ERR_UNSUPPORTED;
+}
+void lsp_batch_destroy(lsp_batch b) { (void)b; }
+
+int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double* grad_v, void* grad_u0,
+                int64_t ckpt_stride, void* stream) {
+  (void)p; (void)dt; (void)nsteps; (void)lamT; (void)grad_v; (void)grad_u0; (void)ckpt_stride; (void)stream;
+  return LSP_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// Internal definitions shared by the translation units of the lattice
+// Strang-splitting library: plan layout, complex helpers, phase-factor
+// encodings and kernel-launch declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "lsp.h"
+
+namespace lsp {
+
+// --------------------------------------------------------------------------
+// Geometry limits
+// --------------------------------------------------------------------------
+// Multipass tiles: a CTA owns TILE elements (16 per thread).  c64 tiles hold
+// 8192 elements (64 KiB), c128 tiles 4096 (64 KiB).
+constexpr int kTileC64 = 8192;
+constexpr int kThreadsC64 = 512;
+constexpr int kTileC128 = 4096;
+constexpr int kThreadsC128 = 256;
+// Column tiles need at least this many adjacent columns for 64-byte segments.
+constexpr int kMinColsC64 = 8;
+constexpr int kMinColsC128 = 4;
+// SMEM-resident path: two state copies must fit in shared memory.
+constexpr int kSmallSmemBytes = 200 * 1024;
+constexpr int kSmallThreads = 512;
+// Bounded device-side waits (grid barrier): spins of ~100 ns each.
+constexpr long long kSpinLimit = 1ll << 25;
+
+enum PathKind { kPathMultipass = 0, kPathSmall = 1 };
+
+// --------------------------------------------------------------------------
+// Plan
+// --------------------------------------------------------------------------
+struct SmallAxis {
+  int len;          // axis length n_i
+  int stride;       // element stride of the axis in kappa / chi order
+  int nfac;         // radix factors of len, applied in order
+  int fac[24];
+  int tw_off;       // offset of this axis' twiddle table in tw_small
+};
+
+}  // namespace lsp
+
+struct lsp_plan_s {
+  int device = 0;
+  int d = 0, r = 0;
+  int64_t n[2] = {1, 1};
+  int64_t ntot = 0;
+  std::vector<int64_t> Z;        // d*r, row-major (component j of z_i at j*r + i)
+  int prec = LSP_C64;
+  double gamma = 1.0;
+  int aa_mode = LSP_AA_MINL2;
+  int path = lsp::kPathSmall;
+
+  // multipass geometry (rank-1, n = N1 * N2, row length N1 contiguous)
+  int logn = 0, N1 = 1, N2 = 1, logN1 = 0, logN2 = 0, logLmax = 0;
+
+  // SMEM-resident geometry
+  int naxes = 0;
+  lsp::SmallAxis axes[2];
+
+  // device buffers
+  void* u = nullptr;          // state, n complex (plan precision)
+  double* v = nullptr;        // potential samples
+  int32_t* norm2 = nullptr;   // ||h_chi||^2 in chi order
+  void* Ph = nullptr;         // exp(-i dt v / (2 gamma)), kappa order, encoded
+  void* Pf = nullptr;         // exp(-i dt v / gamma), kappa order, encoded
+  void* K = nullptr;          // exp(-i gamma 2 pi^2 |h|^2 dt) in the kernel's bin order
+  void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (multipass)
+  void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (multipass)
+  void* tw_small = nullptr;   // per-axis W_len^k tables (SMEM-resident path)
+  void* stage = nullptr;      // n complex128 staging buffer (conversions, spectral output)
+  void* work = nullptr;       // n complex (plan precision): scratch copy for spectral output
+  void* desc = nullptr;       // device copies of the multipass kernel descriptors
+  int* err_host = nullptr;    // pinned mirror of the device error word
+  unsigned* bar = nullptr;    // grid-barrier counter
+  int* err = nullptr;         // device error word
+  size_t bytes = 0;
+
+  int dp_box = 0;
+  int64_t max_norm2 = 0;
+  double tables_dt = 0.0;     // dt of the current phase tables (NaN: none)
+  bool tables_valid = false;
+};
+
+struct lsp_batch_s {
+  std::vector<lsp_plan> plans;
+  int prec = LSP_C64;
+  int device = 0;
+  void* dev_inst = nullptr;   // device copy of the per-instance descriptors
+  int2* dev_colmap = nullptr; // tile -> (instance, local tile)
+  int2* dev_rowmap = nullptr;
+  int total_col = 0, total_row = 0;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  std::vector<int> small_ids; // instances on the SMEM-resident path
+  std::vector<int> multi_ids; // instances on the multipass path
+};
+
+namespace lsp {
+
+// --------------------------------------------------------------------------
+// Complex helpers
+// --------------------------------------------------------------------------
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+__device__ __forceinline__ float2 cmake(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 cmake(double a, double b) { return make_double2(a, b); }
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { return cmake(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { return cmake(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ T cscale(T a, decltype(a.x) s) { return cmake(a.x * s, a.y * s); }
+// a * b
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  return cmake(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ T cmulc(T a, T b) {
+  return cmake(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// a * (DIR * i):  DIR = -1 -> -i,  DIR = +1 -> +i
+template <int DIR, typename T> __device__ __forceinline__ T cmul_i(T a) {
+  return DIR < 0 ? cmake(a.y, -a.x) : cmake(-a.y, a.x);
+}
+
+// --------------------------------------------------------------------------
+// Phase-factor encodings (applied as u <- w u)
+// --------------------------------------------------------------------------
+// complex128: (cos, sin) in FP64.
+// complex64 : w = (-1)^h (1 + c + i s) stored as (c', s) in FP32 with
+//   c = cos(phi) - 1 <= 0 (accurate for small phi), |phi| <= pi/2, and the
+//   half-turn flag h in the sign bit of c' (sign set <=> h = 0).  Keeping
+//   w - 1 instead of cos(phi) avoids the |w| > 1 bias that rounding cos(phi)
+//   to 1 would give for small angles; applying it costs the same four FMAs.
+__host__ __device__ inline void encode_phase(double turns, double2* out) {
+  double r = turns - rint(turns);            // [-1/2, 1/2]
+#ifdef __CUDA_ARCH__
+  double s, c;
+  sincospi(2.0 * r, &s, &c);
+#else
+  double s = sin(2.0 * 3.14159265358979323846 * r), c = cos(2.0 * 3.14159265358979323846 * r);
+#endif
+  *out = double2{c, s};
+}
+
+__host__ __device__ inline void encode_phase(double turns, float2* out) {
+  double r = turns - rint(turns);            // [-1/2, 1/2]
+  int h = 0;
+  if (r > 0.25) { r -= 0.5; h = 1; }
+  else if (r < -0.25) { r += 0.5; h = 1; }
+#ifdef __CUDA_ARCH__
+  double sh = sinpi(r);                      // sin(phi/2), phi = 2 pi r
+  double s = sinpi(2.0 * r);
+#else
+  double sh = sin(3.14159265358979323846 * r);
+  double s = sin(2.0 * 3.14159265358979323846 * r);
+#endif
+  double c = -2.0 * sh * sh;                 // cos(phi) - 1
+  float af = fabsf((float)c);                // |c|, +0.0 when c is -0.0
+  float stored = h ? af : -af;               // sign bit set <=> h = 0 (also -0.0)
+  *out = float2{stored, (float)s};
+}
+
+__device__ __forceinline__ float2 apply_phase(float2 x, float2 e) {
+  unsigned cb = __float_as_uint(e.x);
+  float c = __uint_as_float(cb | 0x80000000u);          // -|c'|
+  unsigned flip = (~cb) & 0x80000000u;                   // h = 1 -> negate
+  float yr = fmaf(x.x, c, fmaf(-x.y, e.y, x.x));
+  float yi = fmaf(x.y, c, fmaf(x.x, e.y, x.y));
+  return make_float2(__uint_as_float(__float_as_uint(yr) ^ flip),
+                     __uint_as_float(__float_as_uint(yi) ^ flip));
+}
+__device__ __forceinline__ double2 apply_phase(double2 x, double2 e) { return cmul(x, e); }
+
+// --------------------------------------------------------------------------
+// Launch entry points implemented in the kernel translation units
+// --------------------------------------------------------------------------
+int multipass_desc_bytes(int prec);
+int multipass_upload_desc(lsp_plan p, cudaStream_t s);
+int multipass_steps(lsp_plan p, int64_t nsteps, cudaStream_t s);
+int multipass_spectral(lsp_plan p, cudaStream_t s);       // -> p->stage (chi order, c128)
+int small_steps(lsp_plan p, int64_t nsteps, cudaStream_t s);
+int small_spectral(lsp_plan p, cudaStream_t s);           // -> p->stage (chi order, c128)
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; }
+
+}  // namespace lsp
+
+#define LSP_CUDA_TRY(call)                                   \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return LSP_ERR_CUDA;              \
+  } while (0)

@@ -1,0 +1,49 @@
+"""The C-ABI library builds, loads and exports every symbol include/lsp.h declares (no GPU)."""
+
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lsp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("lsp_plan_create", "lsp_set_potential", "lsp_set_state", "lsp_strang_steps",
+              "lsp_get_state", "lsp_plan_destroy", "lsp_strerror", "lsp_batch_create",
+              "lsp_batch_steps", "lsp_adjoint", "lsp_lattice_points", "lsp_index_table"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1808_06357_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_strerror_without_gpu():
+    import paper_1808_06357_gb300 as lsp
+    assert lsp.strerror(0) == "ok"
+    assert "canonical" in lsp.strerror(-2)
+    assert lsp.strerror(12345) == "unknown status"
+
+
+def test_plan_create_fails_loudly_without_gpu():
+    """With no usable device the binding raises; nothing falls back to the CPU."""
+    import numpy as np
+    import pytest
+    import torch
+    import paper_1808_06357_gb300 as lsp
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lsp.LspError) as e:
+        lsp.Plan(np.array([1, 5]), (64,), 0.1)
+    assert e.value.code == -6

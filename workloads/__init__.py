@@ -321,12 +321,12 @@ _C2_CACHE = {}
 
 
 def c2(n_log2: int = 22) -> Instance:
-    """C2; below n = 2^20 the hyperbolic cross HC(64) (51,233 elements) cannot be
-    injective, so smaller variants use a seeded random rank-1 lattice."""
+    """C2; below n = 2^22 an HC(64)-injective lattice (51,233 elements) is hard or
+    impossible to find, so smaller variants use a seeded random rank-1 lattice."""
     d = 6
     n = 1 << n_log2
     if n_log2 not in _C2_CACHE:
-        if n_log2 >= 20:
+        if n_log2 >= 22:
             _C2_CACHE[n_log2] = reconstructing_rank1(hyperbolic_cross(d, 64), n, Rng(0, 2))
         else:
             _C2_CACHE[n_log2] = random_rank1(d, n, Rng(n_log2, 2))
