@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 side measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--log2n", type=int, default=22, help="lattice size 2^m of the d=6 workload (profiling)")
+    ap.add_argument("--inner", type=int, default=STEPS_PER_CALL, help="Strang steps per bench step")
     return ap.parse_args()
 
 
@@ -129,10 +131,9 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def c2_inputs():
+def c2_inputs(m: int = 22):
     import workloads as w
-    inst = w.c2(22)
-    return inst
+    return w.c2(m)
 
 
 def cpu_oracle_rate(inst, budget_s: float = 15.0):
@@ -200,7 +201,9 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    inst = c2_inputs()
+    global STEPS_PER_CALL
+    STEPS_PER_CALL = args.inner
+    inst = c2_inputs(args.log2n)
     n = inst.npoints
 
     # inputs: lattice points from the library, input functions from the workload module

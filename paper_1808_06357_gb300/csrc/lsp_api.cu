@@ -209,8 +209,10 @@ static void factorize(int len, SmallAxis& ax) {
   if (rem > 1 && ax.nfac < 24) ax.fac[ax.nfac++] = rem;
 }
 
-template <typename T> static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long long denom) {
-  // entries exp(-2 pi i k / denom), k < len
+template <typename T>
+static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long long denom, bool lo = false) {
+  // entries exp(-2 pi i k / denom), k < len (lo: the rounding residue of each entry)
+  using R = decltype(T{}.x);
   size_t off = buf.size();
   buf.resize(off + (size_t)len * sizeof(T));
   T* t = (T*)(buf.data() + off);
@@ -220,8 +222,33 @@ template <typename T> static void fill_twiddles(std::vector<unsigned char>& buf,
     double f = (double)kk / (double)denom;
     if (f > 0.5) f -= 1.0;
     double ang = -2.0 * M_PI * f;
-    t[k].x = (decltype(t[k].x))cos(ang);
-    t[k].y = (decltype(t[k].y))sin(ang);
+    double c = cos(ang), s = sin(ang);
+    R ch = (R)c, sh = (R)s;
+    t[k].x = lo ? (R)(c - (double)ch) : ch;
+    t[k].y = lo ? (R)(s - (double)sh) : sh;
+  }
+}
+
+// Per-pass twiddle tables of a line of length 2^logL (radix plan R1, 16, ..., 16):
+// pass S >= 2 with span Ns stores W_{16 Ns}^{jm r} at [r-1][jm], r = 1..15, jm < Ns.
+template <typename T> static void fill_pass_twiddles(std::vector<unsigned char>& buf, int logL) {
+  using R = decltype(T{}.x);
+  const int logR1 = logL % 4 == 0 ? 4 : logL % 4;
+  const int P = (logL - logR1) / 4 + 1;
+  for (int S = 2; S <= P; ++S) {
+    const long long Ns = 1ll << (logR1 + 4 * (S - 2)), den = 16 * Ns;
+    for (int r = 1; r < 16; ++r) {
+      for (long long jm = 0; jm < Ns; ++jm) {
+        double f = (double)((jm * r) % den) / (double)den;
+        if (f > 0.5) f -= 1.0;
+        T e;
+        e.x = (R)cos(-2.0 * M_PI * f);
+        e.y = (R)sin(-2.0 * M_PI * f);
+        size_t off = buf.size();
+        buf.resize(off + sizeof(T));
+        memcpy(buf.data() + off, &e, sizeof(T));
+      }
+    }
   }
 }
 
@@ -230,7 +257,7 @@ static void free_plan(lsp_plan p) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
-  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->tw_line, p->tw_fine, p->tw_small,
+  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->tw_line, p->tw_fine, p->tw_pass, p->tw_small,
                   p->stage, p->work, p->desc, p->bar, p->err};
   for (void* b : bufs) if (b) cudaFree(b);
   if (p->err_host) cudaFreeHost(p->err_host);
@@ -304,10 +331,10 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   const int logn = ilog2exact(ntot);
   const bool small_fits = 2 * (size_t)ntot * sz <= (size_t)kSmallSmemBytes;
   if (r == 1 && logn >= 13) {
-    const int maxN1 = prec == LSP_C64 ? 13 : 12;
+    // four-step split N2 = 2^min(10, m/2) (column), N1 = n / N2 (row); one kernel per m
     int logN2 = std::min(10, logn / 2);
     int logN1 = logn - logN2;
-    if (logN1 > maxN1) { free_plan(p); return LSP_ERR_TOO_LARGE; }
+    if (!multipass_supports(prec, logn)) { free_plan(p); return LSP_ERR_TOO_LARGE; }
     p->path = kPathMultipass;
     p->logn = logn; p->logN1 = logN1; p->logN2 = logN2; p->N1 = 1 << logN1; p->N2 = 1 << logN2;
     p->logLmax = std::max(logN1, logN2);
@@ -356,11 +383,22 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
     if (prec == LSP_C64) fill_twiddles<float2>(tw, nfine, ntot); else fill_twiddles<double2>(tw, nfine, ntot);
     if ((rc = dalloc(p, &p->tw_fine, tw.size()))) return fail(rc);
     if (cudaMemcpy(p->tw_fine, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
+    tw.clear();
+    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN1); else fill_pass_twiddles<double2>(tw, p->logN1);
+    p->twr_entries = (int)(tw.size() / sz);
+    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN2); else fill_pass_twiddles<double2>(tw, p->logN2);
+    if ((rc = dalloc(p, &p->tw_pass, std::max<size_t>(tw.size(), 16)))) return fail(rc);
+    if (cudaMemcpy(p->tw_pass, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
   } else {
     for (int i = 0; i < p->naxes; ++i) {
       p->axes[i].tw_off = (int)(tw.size() / sz);
       if (prec == LSP_C64) fill_twiddles<float2>(tw, p->axes[i].len, p->axes[i].len);
       else fill_twiddles<double2>(tw, p->axes[i].len, p->axes[i].len);
+    }
+    if (prec == LSP_C64) {
+      // lo parts: exact value minus its FP32 rounding, same layout after the hi parts
+      p->tw_lo = (int)(tw.size() / sz);
+      for (int i = 0; i < p->naxes; ++i) fill_twiddles<float2>(tw, p->axes[i].len, p->axes[i].len, true);
     }
     if ((rc = dalloc(p, &p->tw_small, tw.size()))) return fail(rc);
     if (cudaMemcpy(p->tw_small, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);

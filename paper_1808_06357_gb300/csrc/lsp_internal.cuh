@@ -62,6 +62,7 @@ struct lsp_plan_s {
   // SMEM-resident geometry
   int naxes = 0;
   lsp::SmallAxis axes[2];
+  int tw_lo = 0;              // complex64: offset of the lo parts of tw_small
 
   // device buffers
   void* u = nullptr;          // state, n complex (plan precision)
@@ -72,6 +73,8 @@ struct lsp_plan_s {
   void* K = nullptr;          // exp(-i gamma 2 pi^2 |h|^2 dt) in the kernel's bin order
   void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (multipass)
   void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (multipass)
+  void* tw_pass = nullptr;    // per-pass line twiddles: row lines, then column lines
+  int twr_entries = 0;        // entries of the row-line part of tw_pass
   void* tw_small = nullptr;   // per-axis W_len^k tables (SMEM-resident path)
   void* stage = nullptr;      // n complex128 staging buffer (conversions, spectral output)
   void* work = nullptr;       // n complex (plan precision): scratch copy for spectral output
@@ -181,6 +184,7 @@ __device__ __forceinline__ double2 apply_phase(double2 x, double2 e) { return cm
 // Launch entry points implemented in the kernel translation units
 // --------------------------------------------------------------------------
 int multipass_desc_bytes(int prec);
+bool multipass_supports(int prec, int m);
 int multipass_upload_desc(lsp_plan p, cudaStream_t s);
 int multipass_steps(lsp_plan p, int64_t nsteps, cudaStream_t s);
 int multipass_spectral(lsp_plan p, cudaStream_t s);       // -> p->stage (chi order, c128)

@@ -21,16 +21,18 @@ template <typename T> struct SmallDesc {
   const T* Ph;
   const T* Pf;
   const T* K;        // chi order
-  const T* tw;       // per-axis W_len^k tables
+  const T* tw;       // per-axis W_len^k tables (complex64: hi parts, then lo parts)
   double2* spec;     // spectral output (chi order)
+  int tw_lo;         // offset of the lo parts (complex64)
   int n;
   int naxes;
   SmallAxis axes[2];
-  R inv_n;
+  R inv_n;           // 1/n rounded
+  R inv_n_lo;        // 1/n - inv_n
 };
 
 template <int DIR, typename T>
-__device__ void small_pass(const SmallAxis& ax, const T* tw, int R, int Ns, int n, const T* x, T* y) {
+__device__ void small_pass(const SmallAxis& ax, const T* tw, int tw_lo, int R, int Ns, int n, const T* x, T* y) {
   const int len = ax.len, st = ax.stride;
   const int m = len / (Ns * R);          // len / (Ns R)
   const int lenR = len / R;
@@ -52,7 +54,17 @@ __device__ void small_pass(const SmallAxis& ax, const T* tw, int R, int Ns, int 
       T xv = x[base + (j + r * lenR) * st];
       T w = __ldg(tw + ax.tw_off + kk * m);
       if (DIR > 0) w.y = -w.y;
-      acc = cadd(acc, cmul(xv, w));
+      if constexpr (sizeof(T) == 8) {
+        // FP32: twiddle as hi + lo so the fixed rounding of each table entry
+        // does not accumulate over the steps
+        T wl = __ldg(tw + tw_lo + ax.tw_off + kk * m);
+        if (DIR > 0) wl.y = -wl.y;
+        const float tr = fmaf(xv.x, wl.x, -xv.y * wl.y), ti = fmaf(xv.x, wl.y, xv.y * wl.x);
+        acc.x = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, acc.x + tr));
+        acc.y = fmaf(xv.x, w.y, fmaf(xv.y, w.x, acc.y + ti));
+      } else {
+        acc = cadd(acc, cmul(xv, w));
+      }
       kk += step;
       if (kk >= NsR) kk -= NsR;
     }
@@ -69,7 +81,7 @@ __device__ T* small_dft(const SmallDesc<T>& S, T* a, T* b) {
     const SmallAxis& ax = S.axes[ai];
     int Ns = 1;
     for (int f = 0; f < ax.nfac; ++f) {
-      small_pass<DIR>(ax, S.tw, ax.fac[f], Ns, S.n, src, dst);
+      small_pass<DIR>(ax, S.tw, S.tw_lo, ax.fac[f], Ns, S.n, src, dst);
       __syncthreads();
       Ns *= ax.fac[f];
       T* t = src; src = dst; dst = t;
@@ -108,8 +120,13 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const SmallDesc<T>
     oth = cur == a ? b : a;
     cur = small_dft<+1>(S, cur, oth);
     const T* P = step + 1 < nsteps ? S.Pf : S.Ph;
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
-      cur[k] = apply_phase(cscale(cur[k], S.inv_n), __ldg(P + k));
+    // 1/n as hi + lo: for n not a power of two a rounded 1/n would scale the
+    // norm by the same factor every step
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      T x = cur[k];
+      x = cmake(fma(x.x, S.inv_n, x.x * S.inv_n_lo), fma(x.y, S.inv_n, x.y * S.inv_n_lo));
+      cur[k] = apply_phase(x, __ldg(P + k));
+    }
     __syncthreads();
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) S.u[k] = cur[k];
@@ -122,12 +139,14 @@ template <typename T> static SmallDesc<T> make_small(lsp_plan p) {
   S.Pf = (const T*)p->Pf;
   S.K = (const T*)p->K;
   S.tw = (const T*)p->tw_small;
+  S.tw_lo = p->tw_lo;
   S.spec = (double2*)p->stage;
   S.n = (int)p->ntot;
   S.naxes = p->naxes;
   S.axes[0] = p->axes[0];
   S.axes[1] = p->axes[1];
   S.inv_n = (decltype(S.inv_n))(1.0 / (double)p->ntot);
+  S.inv_n_lo = (decltype(S.inv_n))(1.0 / (double)p->ntot - (double)S.inv_n);
   return S;
 }
 

@@ -1,19 +1,20 @@
 // Tile FFT building blocks for the multipass Strang step.
 //
-// A CTA owns a tile of C lines of length L (16 * NT elements).  Lines are
-// either rows (contiguous, "line-major" thread mapping: consecutive threads
-// take consecutive elements of a line) or columns (stride N1, "line-minor":
-// consecutive threads take consecutive lines, i.e. adjacent columns).
+// A CTA owns a tile of C lines of length L, C * L = 16 * NT elements (16 per
+// thread).  Lines are rows (contiguous; "major" thread mapping: consecutive
+// threads take consecutive elements of one line) or columns (stride N1;
+// consecutive threads take adjacent columns).  L, C and the radix plan are
+// compile-time constants so that every index, shift and shared-memory offset
+// folds into immediates.
 //
-// Line transforms are Stockham decimation-in-time passes (paper eq. Fnx, the
-// O(n log n) FFT of Sec. 2.2): pass s has radix R_s and span Ns_s; butterfly j
+// Line transforms are Stockham decimation-in-time passes (the O(n log n)
+// FFT of Sec. 2.2, eq. Fnx): pass s has radix R_s and span Ns_s; butterfly j
 // reads x[j + r L/R], applies W_{Ns R}^{(j mod Ns) r}, does a radix-R DFT and
-// writes y[(j/Ns) Ns R + (j mod Ns) + s Ns].  The radix plan is R_1 in
-// {2,4,8,16} then radix 16, so the last pass is always radix 16.
-// The inverse transform runs the same passes backward, each one the
-// conjugate transpose of its forward pass (butterfly, then conjugate
-// twiddle), so the inverse's output pattern equals the forward's input
-// pattern and the two meet in registers with no shared-memory round trip.
+// writes y[(j/Ns) Ns R + (j mod Ns) + t Ns].  The radix plan is R_1 in
+// {2,4,8,16} followed by radix-16 passes, so the last pass is radix 16.
+// The inverse runs the passes backward, each the conjugate transpose of its
+// forward pass (butterfly, then conjugate twiddle), so the inverse's output
+// pattern equals the forward's input pattern: the two meet in registers.
 #pragma once
 
 #include "lsp_internal.cuh"
@@ -44,7 +45,6 @@ template <typename R> struct KC {
 // x * exp(DIR * i * pi / 4)
 template <int DIR, typename T> __device__ __forceinline__ T mul_w8(T x) {
   using R = decltype(x.x);
-  // (1 + DIR i)/sqrt(2): (xr - DIR xi, xi + DIR xr) / sqrt(2)
   R a = DIR < 0 ? x.x + x.y : x.x - x.y;
   R b = DIR < 0 ? x.y - x.x : x.y + x.x;
   return cmake(mulk(a, KC<R>::r2h, KC<R>::r2l), mulk(b, KC<R>::r2h, KC<R>::r2l));
@@ -52,33 +52,35 @@ template <int DIR, typename T> __device__ __forceinline__ T mul_w8(T x) {
 // x * exp(DIR * i * 3 pi / 4)
 template <int DIR, typename T> __device__ __forceinline__ T mul_w8_3(T x) {
   using R = decltype(x.x);
-  // (-1 + DIR i)/sqrt(2): (-xr - DIR xi, -xi + DIR xr) / sqrt(2)
   R a = DIR < 0 ? x.y - x.x : -x.x - x.y;
   R b = DIR < 0 ? -x.y - x.x : x.x - x.y;
   return cmake(mulk(a, KC<R>::r2h, KC<R>::r2l), mulk(b, KC<R>::r2h, KC<R>::r2l));
 }
-// x * (c + DIR i s) for the (cos, sin) pair given as hi/lo parts
-__device__ __forceinline__ float2 mul_cs(float2 x, float ch, float cl, float sh, float sl, int dir) {
-  float s_h = dir < 0 ? -sh : sh, s_l = dir < 0 ? -sl : sl;
+// x * (c + DIR i s) for a (cos, sin) pair given as hi/lo parts
+template <int DIR>
+__device__ __forceinline__ float2 mul_cs(float2 x, float ch, float cl, float sh, float sl) {
+  const float s_h = DIR < 0 ? -sh : sh, s_l = DIR < 0 ? -sl : sl;
   float re = fmaf(x.x, ch, fmaf(-x.y, s_h, fmaf(x.x, cl, -x.y * s_l)));
   float im = fmaf(x.x, s_h, fmaf(x.y, ch, fmaf(x.x, s_l, x.y * cl)));
   return make_float2(re, im);
 }
-__device__ __forceinline__ double2 mul_cs(double2 x, double ch, double, double sh, double, int dir) {
-  double s = dir < 0 ? -sh : sh;
+template <int DIR>
+__device__ __forceinline__ double2 mul_cs(double2 x, double ch, double, double sh, double) {
+  const double s = DIR < 0 ? -sh : sh;
   return make_double2(fma(x.x, ch, -x.y * s), fma(x.x, s, x.y * ch));
 }
 // x * exp(DIR * i * 2 pi k / 16) for k in {1, 3, 9}
 template <int DIR, int K, typename T> __device__ __forceinline__ T mul_w16(T x) {
   using R = decltype(x.x);
-  if (K == 1) return mul_cs(x, KC<R>::c1h, KC<R>::c1l, KC<R>::s1h, KC<R>::s1l, DIR);
-  if (K == 3) return mul_cs(x, KC<R>::s1h, KC<R>::s1l, KC<R>::c1h, KC<R>::c1l, DIR);
-  // K == 9: -exp(DIR i pi/8)
-  T y = mul_cs(x, KC<R>::c1h, KC<R>::c1l, KC<R>::s1h, KC<R>::s1l, DIR);
-  return cmake(-y.x, -y.y);
+  if constexpr (K == 1) return mul_cs<DIR>(x, KC<R>::c1h, KC<R>::c1l, KC<R>::s1h, KC<R>::s1l);
+  else if constexpr (K == 3) return mul_cs<DIR>(x, KC<R>::s1h, KC<R>::s1l, KC<R>::c1h, KC<R>::c1l);
+  else {  // K == 9: -exp(DIR i pi/8)
+    T y = mul_cs<DIR>(x, KC<R>::c1h, KC<R>::c1l, KC<R>::s1h, KC<R>::s1l);
+    return cmake(-y.x, -y.y);
+  }
 }
 
-template <int DIR, typename T> __device__ __forceinline__ void bfly2(T& a, T& b) {
+template <typename T> __device__ __forceinline__ void bfly2(T& a, T& b) {
   T t = a; a = cadd(t, b); b = csub(t, b);
 }
 template <int DIR, typename T> __device__ __forceinline__ void bfly4(T& a0, T& a1, T& a2, T& a3) {
@@ -86,34 +88,31 @@ template <int DIR, typename T> __device__ __forceinline__ void bfly4(T& a0, T& a
   a0 = cadd(t0, t2); a2 = csub(t0, t2); a1 = cadd(t1, t3); a3 = csub(t1, t3);
 }
 
-// Radix-R DFT of v[0..R-1] in place: y_s = sum_r v_r exp(DIR 2 pi i r s / R).
-// Output s is left in register OUT<R>(s).
-template <int R> struct Out;
-template <> struct Out<2> { static __device__ __forceinline__ constexpr int at(int s) { return s; } };
-template <> struct Out<4> { static __device__ __forceinline__ constexpr int at(int s) { return s; } };
-template <> struct Out<8> { static __device__ __forceinline__ constexpr int at(int s) { return 2 * (s & 3) + (s >> 2); } };
-template <> struct Out<16> { static __device__ __forceinline__ constexpr int at(int s) { return (s >> 2) + 4 * (s & 3); } };
+// Radix-R DFT y_t = sum_r v_r exp(DIR 2 pi i r t / R) in place; output t is
+// left in register out_at<R>(t).
+template <int R> __host__ __device__ constexpr int out_at(int t) {
+  return R == 8 ? 2 * (t & 3) + (t >> 2) : R == 16 ? (t >> 2) + 4 * (t & 3) : t;
+}
 
 template <int R, int DIR, typename T> __device__ __forceinline__ void bfly(T* v) {
   if constexpr (R == 2) {
-    bfly2<DIR>(v[0], v[1]);
+    bfly2(v[0], v[1]);
   } else if constexpr (R == 4) {
     bfly4<DIR>(v[0], v[1], v[2], v[3]);
   } else if constexpr (R == 8) {
-    // r = r1 + 2 r2, s = s2 + 4 s1
+    // r = r1 + 2 r2, t = t2 + 4 t1
     bfly4<DIR>(v[0], v[2], v[4], v[6]);
     bfly4<DIR>(v[1], v[3], v[5], v[7]);
     v[3] = mul_w8<DIR>(v[3]);
     v[5] = cmul_i<DIR>(v[5]);
     v[7] = mul_w8_3<DIR>(v[7]);
-    bfly2<DIR>(v[0], v[1]); bfly2<DIR>(v[2], v[3]); bfly2<DIR>(v[4], v[5]); bfly2<DIR>(v[6], v[7]);
+    bfly2(v[0], v[1]); bfly2(v[2], v[3]); bfly2(v[4], v[5]); bfly2(v[6], v[7]);
   } else {
-    // r = r1 + 4 r2, s = s2 + 4 s1
+    // r = r1 + 4 r2, t = t2 + 4 t1
     bfly4<DIR>(v[0], v[4], v[8], v[12]);
     bfly4<DIR>(v[1], v[5], v[9], v[13]);
     bfly4<DIR>(v[2], v[6], v[10], v[14]);
     bfly4<DIR>(v[3], v[7], v[11], v[15]);
-    // twiddle W16^{r1 s2} on v[r1 + 4 s2]
     v[5] = mul_w16<DIR, 1>(v[5]);
     v[9] = mul_w8<DIR>(v[9]);
     v[13] = mul_w16<DIR, 3>(v[13]);
@@ -130,236 +129,171 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void bfly(T* v)
   }
 }
 
-// ---------------------------------------------------------------------------
-// Tile geometry
-// ---------------------------------------------------------------------------
-struct Geo {
-  int logL;        // line length L = 2^logL
-  int logC;        // lines in the tile
-  int major;       // 1: rows (j fastest over threads), 0: columns (line fastest)
-  int logR1;       // log2 of the first-pass radix
-  int p;           // number of passes
-  int logLmax;     // size of the line-twiddle table
-};
-
 template <typename T> struct Swz;
-template <> struct Swz<float2> {
+template <> struct Swz<float2> {   // 16 x 8 B per 128 B bank row
   static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 4) & 15); }
 };
-template <> struct Swz<double2> {
+template <> struct Swz<double2> {  // 8 x 16 B per 128 B bank row
   static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 3) & 7); }
 };
 
-template <typename T> __device__ __forceinline__ int sidx(const Geo& g, int b, int i) {
-  int e = g.major ? ((b << g.logL) + i) : ((i << g.logC) + b);
-  return Swz<T>::f(e);
-}
-
-// Butterfly beta of a pass with log2(L/R) = lLR -> (line b, butterfly j).
-__device__ __forceinline__ void bmap(const Geo& g, int beta, int lLR, int& b, int& j) {
-  if (g.major) { j = beta & ((1 << lLR) - 1); b = beta >> lLR; }
-  else { b = beta & ((1 << g.logC) - 1); j = beta >> g.logC; }
-}
-
-// log2 of Ns for pass s (1-based): Ns_1 = 1, Ns_s = R1 * 16^(s-2)
-__device__ __forceinline__ int log_ns(const Geo& g, int s) { return s == 1 ? 0 : g.logR1 + 4 * (s - 2); }
-
-template <typename T> __device__ __forceinline__ T ldtw(const T* tw, int k) { return __ldg(tw + k); }
-
 // ---------------------------------------------------------------------------
-// Passes.  Register layout: v[q * R + r] holds element r of the thread's q-th
-// butterfly (16 / R butterflies per thread, 16 elements).
+// Compile-time line geometry
 // ---------------------------------------------------------------------------
+template <typename T, int NT, int LOGL, bool MAJOR>
+struct Line {
+  static constexpr int L = 1 << LOGL;
+  static constexpr int LOGNT = NT == 512 ? 9 : NT == 256 ? 8 : NT == 128 ? 7 : 10;
+  static constexpr int LOGC = LOGNT + 4 - LOGL;      // lines per tile
+  static constexpr int C = 1 << LOGC;
+  static constexpr int LOGR1 = LOGL % 4 == 0 ? 4 : LOGL % 4;
+  static constexpr int R1 = 1 << LOGR1;
+  static constexpr int P = (LOGL - LOGR1) / 4 + 1;   // passes
+  static_assert(LOGC >= 0, "line longer than a tile");
+  static_assert(LOGL >= 4, "line shorter than 16");
 
-// Read pass-s inputs x[j + r L/R] from shared memory.
-template <int R, int NT, typename T>
-__device__ __forceinline__ void read_in(const Geo& g, const T* sm, T (&v)[16]) {
-  constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);
-  const int lLR = g.logL - LR;
-  const int nb = 1 << (g.logC + lLR);
-#pragma unroll
-  for (int q = 0; q < 16 / R; ++q) {
-    int beta = threadIdx.x + NT * q;
-    if (beta < nb) {
-      int b, j; bmap(g, beta, lLR, b, j);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = sm[sidx<T>(g, b, j + (r << lLR))];
-    }
+  // log2 Ns of pass S (1-based)
+  static constexpr int lns(int S) { return S == 1 ? 0 : LOGR1 + 4 * (S - 2); }
+  static constexpr int radix_log(int S) { return S == 1 ? LOGR1 : 4; }
+  // Per-pass twiddle tables: pass S >= 2 (radix 16) owns 15 Ns entries laid
+  // out [r-1][jm] = W_{16 Ns}^{jm r}, so that threads with consecutive jm read
+  // consecutive words.  tw_off(S) is the start of pass S's table.
+  static constexpr int tw_off(int S) {
+    int o = 0;
+    for (int s = 2; s < S; ++s) o += 15 << lns(s);
+    return o;
   }
-}
+  static constexpr int TW_ENTRIES = tw_off(P + 1);
 
-// Forward pass s body on registers: twiddle (s > 1) then butterfly.
-template <int R, int NT, typename T>
-__device__ __forceinline__ void fwd_body(const Geo& g, int s, const T* twl, T (&v)[16]) {
-  constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);
-  const int lLR = g.logL - LR;
-  const int nb = 1 << (g.logC + lLR);
-  const int lns = log_ns(g, s);
+  // q-th butterfly of this thread for radix 2^LR -> (line b, butterfly j)
+  template <int LR>
+  static __device__ __forceinline__ void bm(int q, int& b, int& j) {
+    const int beta = threadIdx.x + NT * q;
+    if constexpr (MAJOR) { j = beta & ((1 << (LOGL - LR)) - 1); b = beta >> (LOGL - LR); }
+    else { b = beta & (C - 1); j = beta >> LOGC; }
+  }
+  static __device__ __forceinline__ int sidx(int b, int i) {
+    return Swz<T>::f(MAJOR ? (b << LOGL) + i : (i << LOGC) + b);
+  }
+
+  // ---- forward pass S: registers hold inputs x[j + r L/R] ----
+  template <int S>
+  static __device__ __forceinline__ void fwd_body(const T* __restrict__ tw, T (&v)[16]) {
+    constexpr int LR = radix_log(S), R = 1 << LR, LNS = lns(S);
 #pragma unroll
-  for (int q = 0; q < 16 / R; ++q) {
-    int beta = threadIdx.x + NT * q;
-    if (beta < nb) {
-      if (s > 1) {
-        int b, j; bmap(g, beta, lLR, b, j);
-        int jm = j & ((1 << lns) - 1);
-        int sh = g.logLmax - lns - LR;
+    for (int q = 0; q < 16 / R; ++q) {
+      if constexpr (S > 1) {
+        int b, j; bm<LR>(q, b, j);
+        const T* tq = tw + tw_off(S) + (j & ((1 << LNS) - 1));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], ldtw(twl, (jm * r) << sh));
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tq[(r - 1) << LNS]);
       }
       bfly<R, -1>(&v[q * R]);
     }
   }
-}
-
-// Write forward pass-s outputs y[(j/Ns) Ns R + (j mod Ns) + s Ns] to shared memory.
-template <int R, int NT, typename T>
-__device__ __forceinline__ void write_out(const Geo& g, int s, T* sm, const T (&v)[16]) {
-  constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);
-  const int lLR = g.logL - LR;
-  const int nb = 1 << (g.logC + lLR);
-  const int lns = log_ns(g, s);
+  template <int S>
+  static __device__ __forceinline__ void write_out(T* sm, const T (&v)[16]) {
+    constexpr int LR = radix_log(S), R = 1 << LR, LNS = lns(S);
 #pragma unroll
-  for (int q = 0; q < 16 / R; ++q) {
-    int beta = threadIdx.x + NT * q;
-    if (beta < nb) {
-      int b, j; bmap(g, beta, lLR, b, j);
-      int jm = j & ((1 << lns) - 1);
-      int ob = ((j >> lns) << (lns + LR)) + jm;
+    for (int q = 0; q < 16 / R; ++q) {
+      int b, j; bm<LR>(q, b, j);
+      const int ob = ((j >> LNS) << (LNS + LR)) + (j & ((1 << LNS) - 1));
 #pragma unroll
-      for (int t = 0; t < R; ++t) sm[sidx<T>(g, b, ob + (t << lns))] = v[q * R + Out<R>::at(t)];
+      for (int t = 0; t < R; ++t) sm[sidx(b, ob + (t << LNS))] = v[q * R + out_at<R>(t)];
     }
   }
-}
-
-// Read inverse pass-s inputs (the forward pass' output positions) into natural order.
-template <int R, int NT, typename T>
-__device__ __forceinline__ void read_out(const Geo& g, int s, const T* sm, T (&v)[16]) {
-  constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);
-  const int lLR = g.logL - LR;
-  const int nb = 1 << (g.logC + lLR);
-  const int lns = log_ns(g, s);
+  template <int S>
+  static __device__ __forceinline__ void read_in(const T* sm, T (&v)[16]) {
+    constexpr int LR = radix_log(S), R = 1 << LR;
 #pragma unroll
-  for (int q = 0; q < 16 / R; ++q) {
-    int beta = threadIdx.x + NT * q;
-    if (beta < nb) {
-      int b, j; bmap(g, beta, lLR, b, j);
-      int jm = j & ((1 << lns) - 1);
-      int ob = ((j >> lns) << (lns + LR)) + jm;
+    for (int q = 0; q < 16 / R; ++q) {
+      int b, j; bm<LR>(q, b, j);
 #pragma unroll
-      for (int t = 0; t < R; ++t) v[q * R + t] = sm[sidx<T>(g, b, ob + (t << lns))];
+      for (int r = 0; r < R; ++r) v[q * R + r] = sm[sidx(b, j + (r << (LOGL - LR)))];
     }
   }
-}
-
-// Inverse pass-s body: butterfly (conjugate) then conjugate twiddle (s > 1).
-// Output element r of butterfly q ends in v[q * R + r] (natural order).
-template <int R, int NT, typename T>
-__device__ __forceinline__ void inv_body(const Geo& g, int s, const T* twl, T (&v)[16]) {
-  constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);
-  const int lLR = g.logL - LR;
-  const int nb = 1 << (g.logC + lLR);
-  const int lns = log_ns(g, s);
+  // ---- inverse pass S (conjugate transpose of forward pass S) ----
+  template <int S>
+  static __device__ __forceinline__ void read_out(const T* sm, T (&v)[16]) {
+    constexpr int LR = radix_log(S), R = 1 << LR, LNS = lns(S);
 #pragma unroll
-  for (int q = 0; q < 16 / R; ++q) {
-    int beta = threadIdx.x + NT * q;
-    if (beta < nb) {
+    for (int q = 0; q < 16 / R; ++q) {
+      int b, j; bm<LR>(q, b, j);
+      const int ob = ((j >> LNS) << (LNS + LR)) + (j & ((1 << LNS) - 1));
+#pragma unroll
+      for (int t = 0; t < R; ++t) v[q * R + t] = sm[sidx(b, ob + (t << LNS))];
+    }
+  }
+  template <int S>
+  static __device__ __forceinline__ void inv_body(const T* __restrict__ tw, T (&v)[16]) {
+    constexpr int LR = radix_log(S), R = 1 << LR, LNS = lns(S);
+#pragma unroll
+    for (int q = 0; q < 16 / R; ++q) {
       T w[R];
 #pragma unroll
       for (int t = 0; t < R; ++t) w[t] = v[q * R + t];
       bfly<R, +1>(w);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = w[Out<R>::at(r)];
-      if (s > 1) {
-        int b, j; bmap(g, beta, lLR, b, j);
-        int jm = j & ((1 << lns) - 1);
-        int sh = g.logLmax - lns - LR;
+      for (int r = 0; r < R; ++r) v[q * R + r] = w[out_at<R>(r)];
+      if constexpr (S > 1) {
+        int b, j; bm<LR>(q, b, j);
+        const T* tq = tw + tw_off(S) + (j & ((1 << LNS) - 1));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[q * R + r] = cmulc(v[q * R + r], ldtw(twl, (jm * r) << sh));
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmulc(v[q * R + r], tq[(r - 1) << LNS]);
       }
     }
   }
-}
-
-// Write inverse pass-s outputs x[j + r L/R] to shared memory.
-template <int R, int NT, typename T>
-__device__ __forceinline__ void write_in(const Geo& g, T* sm, const T (&v)[16]) {
-  constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);
-  const int lLR = g.logL - LR;
-  const int nb = 1 << (g.logC + lLR);
+  template <int S>
+  static __device__ __forceinline__ void write_in(T* sm, const T (&v)[16]) {
+    constexpr int LR = radix_log(S), R = 1 << LR;
 #pragma unroll
-  for (int q = 0; q < 16 / R; ++q) {
-    int beta = threadIdx.x + NT * q;
-    if (beta < nb) {
-      int b, j; bmap(g, beta, lLR, b, j);
+    for (int q = 0; q < 16 / R; ++q) {
+      int b, j; bm<LR>(q, b, j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[sidx<T>(g, b, j + (r << lLR))] = v[q * R + r];
+      for (int r = 0; r < R; ++r) sm[sidx(b, j + (r << (LOGL - LR)))] = v[q * R + r];
     }
   }
-}
 
-// Permute forward-pass outputs held in registers (register Out<R>(t) holds
-// output t) into natural order, so that an inverse pass can consume them.
-template <int R, typename T> __device__ __forceinline__ void out_to_nat(T (&v)[16]) {
-  T w[16];
-#pragma unroll
-  for (int q = 0; q < 16 / R; ++q)
-#pragma unroll
-    for (int t = 0; t < R; ++t) w[q * R + t] = v[q * R + Out<R>::at(t)];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = w[i];
-}
-
-// Dispatch helpers on the runtime first-pass radix.
-#define LSP_R1_DISPATCH(logR1, ...)                          \
-  switch (logR1) {                                           \
-    case 1: { constexpr int RR = 2; __VA_ARGS__; } break;    \
-    case 2: { constexpr int RR = 4; __VA_ARGS__; } break;    \
-    case 3: { constexpr int RR = 8; __VA_ARGS__; } break;    \
-    default: { constexpr int RR = 16; __VA_ARGS__; } break;  \
-  }
-
-// Radix of pass s (1-based): R1 for s = 1, else 16.
-// Full forward line DFT from registers (loaded in the pass-1 input pattern);
-// ends with the last pass' outputs in registers in natural output order
-// (element j + t L/16 of butterfly q in v[q*16 + t]).
-template <int NT, typename T>
-__device__ __forceinline__ void line_dft(const Geo& g, T* sm, const T* twl, T (&v)[16]) {
-  for (int s = 1; s <= g.p; ++s) {
-    if (s > 1) {
+  // Forward line DFT: registers in the pass-1 input pattern -> last-pass
+  // outputs in natural order (v[t] = element j + t L/16 of the thread's
+  // radix-16 butterfly).
+  template <int S = 1>
+  static __device__ __forceinline__ void dft(T* sm, const T* tw, T (&v)[16]) {
+    if constexpr (S > 1) {
       __syncthreads();
-      read_in<16, NT>(g, sm, v);
-      fwd_body<16, NT>(g, s, twl, v);
+      read_in<S>(sm, v);
+    }
+    fwd_body<S>(tw, v);
+    if constexpr (S < P) {
+      __syncthreads();
+      write_out<S>(sm, v);
+      dft<S + 1>(sm, tw, v);
     } else {
-      LSP_R1_DISPATCH(g.logR1, fwd_body<RR, NT>(g, 1, twl, v));
-    }
-    if (s < g.p) {
-      __syncthreads();                            // earlier readers of sm are done
-      if (s == 1) { LSP_R1_DISPATCH(g.logR1, write_out<RR, NT>(g, 1, sm, v)); }
-      else write_out<16, NT>(g, s, sm, v);
-    }
-  }
-  if (g.p == 1) { LSP_R1_DISPATCH(g.logR1, out_to_nat<RR>(v)); }
-  else out_to_nat<16>(v);
-}
-
-// Full inverse line DFT (unnormalised) from registers holding the last
-// forward pass' outputs in natural order; ends with the pass-1 input pattern
-// in registers.
-template <int NT, typename T>
-__device__ __forceinline__ void line_idft(const Geo& g, T* sm, const T* twl, T (&v)[16]) {
-  for (int s = g.p; s >= 1; --s) {
-    if (s < g.p) {
-      __syncthreads();                            // writes of the previous pass visible
-      if (s == 1) { LSP_R1_DISPATCH(g.logR1, read_out<RR, NT>(g, 1, sm, v)); }
-      else read_out<16, NT>(g, s, sm, v);
-    }
-    if (s == 1) { LSP_R1_DISPATCH(g.logR1, inv_body<RR, NT>(g, 1, twl, v)); }
-    else inv_body<16, NT>(g, s, twl, v);
-    if (s > 1) {
-      __syncthreads();                            // all reads of this pass done
-      write_in<16, NT>(g, sm, v);
+      constexpr int R = 1 << radix_log(S);
+      T w[16];
+#pragma unroll
+      for (int q = 0; q < 16 / R; ++q)
+#pragma unroll
+        for (int t = 0; t < R; ++t) w[q * R + t] = v[q * R + out_at<R>(t)];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = w[i];
     }
   }
-}
+  // Inverse line DFT (unnormalised): registers holding the last forward
+  // pass' outputs in natural order -> the pass-1 input pattern.
+  template <int S = P>
+  static __device__ __forceinline__ void idft(T* sm, const T* tw, T (&v)[16]) {
+    if constexpr (S < P) {
+      __syncthreads();
+      read_out<S>(sm, v);
+    }
+    inv_body<S>(tw, v);
+    if constexpr (S > 1) {
+      __syncthreads();
+      write_in<S>(sm, v);
+      idft<S - 1>(sm, tw, v);
+    }
+  }
+};
 
 }  // namespace lsp
