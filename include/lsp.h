@@ -193,6 +193,33 @@ void lsp_batch_destroy(lsp_batch b);
 int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double* grad_v,
                 void* grad_u0, int64_t ckpt_stride, void* stream);
 
+/*
+ * lsp_strang_steps_noalloc -- nsteps Strang steps of a rank-1 lattice state,
+ * like lsp_strang_steps on a plan, but allocating no device memory at all.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc -- code under an allocator that must own every device byte, a
+ * real-time or embedded loop that may not allocate once running, or a caller
+ * holding no plan.  The phase and twiddle tables it needs live in one fixed
+ * file-scope device array of 640 KiB that every device which loads the library
+ * holds until the process exits.
+ *   prec    LSP_C64 or LSP_C128 (element type of u).
+ *   n       lattice size: 1 <= n <= 8192 (complex64) or <= 6400 (complex128);
+ *           larger n returns LSP_ERR_TOO_LARGE.  Any factorisation of n works.
+ *   gamma, dt, nsteps  as lsp_plan_create / lsp_strang_steps.
+ *   v       n doubles (device): v(p_k) in point order k.
+ *   norm2   n int32 (device): ||h_xi||^2 per bin xi = 0..n-1 (e.g. the values
+ *           lsp_index_norms returns for the same lattice).
+ *   u       n complex (device), read and overwritten in place.
+ * Runs on the current CUDA device, asynchronously on `stream`.  The first call
+ * on a device looks up the device address of the array (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array and rewrites it completely, so calls that overlap on
+ * the GPU (other streams, other threads) race; serialise them.
+ * Errors: BAD_ARG, TOO_LARGE, CUDA.
+ */
+int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, double dt, int64_t nsteps,
+                             const double* v, const int32_t* norm2, void* u, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* lsp_strerror(int code);
 

@@ -54,6 +54,7 @@ def _declare(lib):
         "lsp_batch_steps": (I, [P, P, I64, P]),
         "lsp_batch_destroy": (V, [P]),
         "lsp_adjoint": (I, [P, D, I64, P, P, P, I64, P]),
+        "lsp_strang_steps_noalloc": (I, [I, I64, D, D, I64, P, P, P, P]),
         "lsp_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -250,6 +251,18 @@ class Batch:
             self.destroy()
         except Exception:
             pass
+
+
+def strang_steps_noalloc(u, v, norm2, gamma: float, dt: float, nsteps: int, stream=None):
+    """lsp_strang_steps_noalloc: allocation-free Strang steps on device tensors
+    (u complex64/complex128 updated in place, v float64, norm2 int32)."""
+    lib = load_library()
+    prec = C64 if str(u.dtype).endswith("complex64") else C128
+    up, _ = _buf(u)
+    vp, _ = _buf(v)
+    np_, _ = _buf(norm2)
+    _check(lib.lsp_strang_steps_noalloc(prec, int(u.numel()), float(gamma), float(dt), int(nsteps), vp, np_, up,
+                                        _stream_ptr(stream)), "lsp_strang_steps_noalloc")
 
 
 def adjoint(plan: Plan, dt: float, nsteps: int, lamT, grad_v, grad_u0, ckpt_stride: int = 0, stream=None):

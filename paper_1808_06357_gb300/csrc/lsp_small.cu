@@ -183,3 +183,146 @@ int small_spectral(lsp_plan p, cudaStream_t s) {
 }
 
 }  // namespace lsp
+
+// ===========================================================================
+// Allocation-free entry point: the SMEM-resident Strang loop with its
+// scratch (phase and twiddle tables) in a fixed file-scope device array.
+// For callers that must not allocate device memory -- code running under a
+// host allocator that forbids cudaMalloc, a caller that pre-plans all memory
+// (embedded or real-time use), or a context where an allocation could fail
+// mid-run.  The paper has no counterpart; this is a deployment convenience.
+// ===========================================================================
+namespace lsp {
+
+constexpr long long kNoAllocMaxN = 8192;   // largest lattice (points) the fixed scratch holds
+constexpr int kNoAllocMaxDev = 64;
+
+// Ph[n], Pf[n], K[n], tw[n], tw_lo[n] of the plan precision: 5 * 8192 * 16 B = 640 KiB,
+// held by every device that loads the library until the process exits.
+static __device__ __align__(256) double2 g_noalloc_scratch[5 * kNoAllocMaxN];
+static void* g_noalloc_addr[kNoAllocMaxDev];
+
+template <typename T>
+__global__ void noalloc_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf,
+                               T* K, T* tw, T* twlo, int n, double turns_v, double turns_k) {
+  using R = decltype(T{}.x);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double th = v[i] * turns_v;
+    T a, b, c;
+    encode_phase(th, &a);
+    encode_phase(2.0 * th, &b);
+    encode_phase(turns_k * (double)norm2[i], &c);
+    Ph[i] = a;
+    Pf[i] = b;
+    K[i] = c;
+    // W_n^i = exp(-2 pi i i / n), FP64 then rounded (and its residue for FP32)
+    double s, co;
+    sincospi(-2.0 * (double)i / (double)n, &s, &co);
+    T w, wl;
+    w.x = (R)co;
+    w.y = (R)s;
+    wl.x = (R)(co - (double)w.x);
+    wl.y = (R)(s - (double)w.y);
+    tw[i] = w;
+    if (twlo) twlo[i] = wl;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) small_kernel_noalloc(const __grid_constant__ SmallDesc<T> S,
+                                                                      long long nsteps) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* a = reinterpret_cast<T*>(smraw);
+  T* b = a + S.n;
+  const int n = S.n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = S.u[k];
+  __syncthreads();
+  if (nsteps <= 0) return;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = apply_phase(a[k], S.Ph[k]);
+  __syncthreads();
+  T* cur = a;
+  for (long long step = 0; step < nsteps; ++step) {
+    T* oth = cur == a ? b : a;
+    cur = small_dft<-1>(S, cur, oth);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cur[k] = apply_phase(cur[k], S.K[k]);
+    __syncthreads();
+    oth = cur == a ? b : a;
+    cur = small_dft<+1>(S, cur, oth);
+    const T* P = step + 1 < nsteps ? S.Pf : S.Ph;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      T x = cur[k];
+      x = cmake(fma(x.x, S.inv_n, x.x * S.inv_n_lo), fma(x.y, S.inv_n, x.y * S.inv_n_lo));
+      cur[k] = apply_phase(x, P[k]);
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) S.u[k] = cur[k];
+}
+
+template <typename T>
+static int noalloc_run(void* scratch, long long n, double gamma, double dt, long long nsteps, const double* v,
+                       const int32_t* norm2, void* u, cudaStream_t s) {
+  T* base = (T*)scratch;
+  SmallDesc<T> S{};
+  S.u = (T*)u;
+  S.Ph = base;
+  S.Pf = base + n;
+  S.K = base + 2 * n;
+  S.tw = base + 3 * n;
+  S.tw_lo = (int)n;                       // lo parts follow the n hi parts
+  S.spec = nullptr;
+  S.n = (int)n;
+  S.naxes = 1;
+  S.axes[0].len = (int)n;
+  S.axes[0].stride = 1;
+  S.axes[0].tw_off = 0;
+  S.axes[0].nfac = 0;
+  {
+    int rem = (int)n;
+    const int pref[] = {16, 8, 4, 2};
+    for (int f : pref)
+      while (rem % f == 0 && S.axes[0].nfac < 24) { S.axes[0].fac[S.axes[0].nfac++] = f; rem /= f; }
+    for (int f = 3; f <= rem && S.axes[0].nfac < 24; f += 2)
+      while (rem % f == 0) { S.axes[0].fac[S.axes[0].nfac++] = f; rem /= f; }
+    if (rem > 1) {
+      if (S.axes[0].nfac >= 24) return LSP_ERR_TOO_LARGE;
+      S.axes[0].fac[S.axes[0].nfac++] = rem;
+    }
+  }
+  S.inv_n = (decltype(S.inv_n))(1.0 / (double)n);
+  S.inv_n_lo = (decltype(S.inv_n))(1.0 / (double)n - (double)S.inv_n);
+  const double turns_v = -dt / (4.0 * M_PI * gamma);
+  const double turns_k = -M_PI * gamma * dt;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 64);
+  noalloc_tables<T><<<grid, 256, 0, s>>>(v, norm2, base, base + n, base + 2 * n, base + 3 * n,
+                                         sizeof(T) == 8 ? base + 4 * n : nullptr, (int)n, turns_v, turns_k);
+  LSP_CUDA_TRY(cudaGetLastError());
+  const size_t smem = 2 * (size_t)n * sizeof(T);
+  LSP_CUDA_TRY(cudaFuncSetAttribute(small_kernel_noalloc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  small_kernel_noalloc<T><<<1, kSmallThreads, smem, s>>>(S, nsteps);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lsp
+
+extern "C" int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, double dt, int64_t nsteps,
+                                        const double* v, const int32_t* norm2, void* u, void* stream) {
+  using namespace lsp;
+  if ((prec != LSP_C64 && prec != LSP_C128) || !v || !norm2 || !u) return LSP_ERR_BAD_ARG;
+  if (!(gamma > 0.0) || !isfinite(dt) || nsteps < 0 || n < 1) return LSP_ERR_BAD_ARG;
+  // limits: the fixed scratch (8192 points) and two state copies in shared memory
+  const size_t csz = prec == LSP_C64 ? sizeof(float2) : sizeof(double2);
+  if (n > kNoAllocMaxN || 2 * (size_t)n * csz > (size_t)kSmallSmemBytes) return LSP_ERR_TOO_LARGE;
+  if (nsteps == 0) return LSP_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDev) return LSP_ERR_CUDA;
+  if (!g_noalloc_addr[dev]) {
+    // first call on this device: device address of the file-scope scratch
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LSP_ERR_CUDA;
+    g_noalloc_addr[dev] = ptr;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  return prec == LSP_C64 ? noalloc_run<float2>(g_noalloc_addr[dev], n, gamma, dt, nsteps, v, norm2, u, s)
+                         : noalloc_run<double2>(g_noalloc_addr[dev], n, gamma, dt, nsteps, v, norm2, u, s);
+}
