@@ -165,7 +165,9 @@ int lsp_plan_info(lsp_plan p, int64_t* info);
 
 /*
  * Batched stepping: many independent instances (same precision and device)
- * advanced together by one persistent launch per call.
+ * advanced together.  Instances on the SMEM-resident path share one launch
+ * (one CTA each); multipass instances are grouped by lattice size, one
+ * persistent cooperative launch per size per call.
  *   lsp_batch_create  plans: `count` plan handles (host array, borrowed: the
  *                     plans must outlive the batch).  Errors: BAD_ARG, OOM, CUDA,
  *                     UNSUPPORTED (mixed precision or device).
@@ -175,6 +177,8 @@ int lsp_plan_info(lsp_plan p, int64_t* info);
  */
 int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count);
 int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream);
+/* Synchronise `stream` and return the batch's sticky device status (as lsp_plan_status). */
+int lsp_batch_status(lsp_batch b, void* stream);
 void lsp_batch_destroy(lsp_batch b);
 
 /*

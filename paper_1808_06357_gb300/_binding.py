@@ -53,6 +53,7 @@ def _declare(lib):
         "lsp_batch_create": (I, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), I]),
         "lsp_batch_steps": (I, [P, P, I64, P]),
         "lsp_batch_destroy": (V, [P]),
+        "lsp_batch_status": (I, [P, P]),
         "lsp_adjoint": (I, [P, D, I64, P, P, P, I64, P]),
         "lsp_strang_steps_noalloc": (I, [I, I64, D, D, I64, P, P, P, P]),
         "lsp_strerror": (C.c_char_p, [I]),
@@ -240,6 +241,9 @@ class Batch:
         dt = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
         _check(self._lib.lsp_batch_steps(self._h, C.c_void_p(dt.ctypes.data), int(nsteps), _stream_ptr(stream)),
                "lsp_batch_steps")
+
+    def status(self, stream=None) -> int:
+        return int(self._lib.lsp_batch_status(self._h, _stream_ptr(stream)))
 
     def destroy(self):
         if getattr(self, "_h", None) and self._h.value:

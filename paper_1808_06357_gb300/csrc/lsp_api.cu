@@ -184,6 +184,23 @@ static int launch_convert(const void* src, int sp, void* dst, int dp, long long 
 
 static size_t csize(int prec) { return prec == LSP_C64 ? sizeof(float2) : sizeof(double2); }
 
+// Phase tables of one plan for step size dt (a0), FP64 arguments in turns:
+//   P_half: -dt v / (4 pi gamma),  K: -pi gamma dt ||h||^2.
+int build_phase_tables(lsp_plan p, double dt, cudaStream_t s) {
+  const double turns_v = -dt / (4.0 * M_PI * p->gamma);
+  const double turns_k = -M_PI * p->gamma * dt;
+  const int mp = p->path == kPathMultipass;
+  if (p->prec == LSP_C64)
+    build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
+                                                            (float2*)p->K, p->ntot, turns_v, turns_k, mp, p->logN1,
+                                                            p->logN2);
+  else
+    build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
+                                                              (double2*)p->K, p->ntot, turns_v, turns_k, mp,
+                                                              p->logN1, p->logN2);
+  return cuda_status(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
@@ -492,19 +509,10 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
   if (nsteps == 0) return LSP_OK;
   DeviceGuard g(p->device);
   cudaStream_t s = (cudaStream_t)stream;
-  // phase tables for this dt, FP64 arguments in turns:
-  //   P_half: -dt v / (4 pi gamma),  K: -pi gamma dt ||h||^2
-  const double turns_v = -dt / (4.0 * M_PI * p->gamma);
-  const double turns_k = -M_PI * p->gamma * dt;
+  int rc = build_phase_tables(p, dt, s);
+  if (rc) return rc;
   const int mp = p->path == kPathMultipass;
-  if (p->prec == LSP_C64)
-    build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
-                                                            (float2*)p->K, p->ntot, turns_v, turns_k, mp, p->logN1, p->logN2);
-  else
-    build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
-                                                              (double2*)p->K, p->ntot, turns_v, turns_k, mp, p->logN1, p->logN2);
-  LSP_CUDA_TRY(cudaGetLastError());
-  int rc = mp ? multipass_steps(p, nsteps, s) : small_steps(p, nsteps, s);
+  rc = mp ? multipass_steps(p, nsteps, s) : small_steps(p, nsteps, s);
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return LSP_OK;
@@ -616,17 +624,6 @@ int lsp_plan_info(lsp_plan p, int64_t* info) {
   info[7] = p->max_norm2;
   return LSP_OK;
 }
-
-int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
-  if (out) *out = nullptr;
-  (void)plans; (void)count;
-  return LSP_ERR_UNSUPPORTED;
-}
-int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream) {
-  (void)b; (void)dt; (void)nsteps; (void)stream;
-  return LSP_ERR_UNSUPPORTED;
-}
-void lsp_batch_destroy(lsp_batch b) { (void)b; }
 
 int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double* grad_v, void* grad_u0,
                 int64_t ckpt_stride, void* stream) {

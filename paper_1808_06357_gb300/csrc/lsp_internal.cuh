@@ -91,17 +91,26 @@ struct lsp_plan_s {
 };
 
 struct lsp_batch_s {
-  std::vector<lsp_plan> plans;
+  std::vector<lsp_plan> plans;   // borrowed
   int prec = LSP_C64;
   int device = 0;
-  void* dev_inst = nullptr;   // device copy of the per-instance descriptors
-  int2* dev_colmap = nullptr; // tile -> (instance, local tile)
-  int2* dev_rowmap = nullptr;
-  int total_col = 0, total_row = 0;
-  unsigned* bar = nullptr;
-  int* err = nullptr;
-  std::vector<int> small_ids; // instances on the SMEM-resident path
-  std::vector<int> multi_ids; // instances on the multipass path
+  // SMEM-resident instances: one CTA each, one launch for all of them
+  std::vector<int> small_ids;
+  void* small_desc = nullptr;    // device array of their kernel descriptors
+  int small_max_n = 0;
+  // multipass instances grouped by lattice size 2^m (one kernel per size)
+  struct Class {
+    int m = 0;
+    std::vector<int> ids;
+    void* desc = nullptr;        // device array of descriptors
+    int2* colmap = nullptr;      // sweep tile -> (instance in class, local tile)
+    int2* rowmap = nullptr;
+    int total_col = 0, total_row = 0;
+  };
+  std::vector<Class> classes;
+  unsigned* bar = nullptr;       // grid-barrier counter (reused by every class)
+  int* err = nullptr;            // device error word
+  int* err_host = nullptr;       // pinned mirror
 };
 
 namespace lsp {
@@ -190,6 +199,15 @@ int multipass_steps(lsp_plan p, int64_t nsteps, cudaStream_t s);
 int multipass_spectral(lsp_plan p, cudaStream_t s);       // -> p->stage (chi order, c128)
 int small_steps(lsp_plan p, int64_t nsteps, cudaStream_t s);
 int small_spectral(lsp_plan p, cudaStream_t s);           // -> p->stage (chi order, c128)
+int build_phase_tables(lsp_plan p, double dt, cudaStream_t s);
+// batching hooks: descriptor bytes of a plan, and launches over descriptor arrays
+int small_desc_size(int prec);
+void small_fill_desc(lsp_plan p, void* host_out);
+int small_batch_launch(int prec, const void* ddesc, int count, int max_n, int64_t nsteps, cudaStream_t s);
+int multipass_desc_size(int prec);
+void multipass_fill_desc(lsp_plan p, void* host_out, int* ncol, int* nrow);
+int multipass_batch_steps(int prec, int m, const void* ddesc, const int2* colmap, const int2* rowmap, int ninst,
+                          int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; }
 

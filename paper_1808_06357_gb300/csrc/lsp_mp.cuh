@@ -61,10 +61,15 @@ template <typename T> struct MPParams {
 #ifndef LSP_MINB_C128
 #define LSP_MINB_C128 1
 #endif
-// threads per CTA, elements per tile, minimum resident CTAs per SM (register budget)
+// NT threads per worker, NW workers per CTA, TILE elements per worker tile
+// (16 per thread), minimum resident CTAs per SM (register budget).
 template <typename T> struct Cfg;
-template <> struct Cfg<float2> { static constexpr int NT = kThreadsC64, TILE = kTileC64, MINB = LSP_MINB_C64; };
-template <> struct Cfg<double2> { static constexpr int NT = kThreadsC128, TILE = kTileC128, MINB = LSP_MINB_C128; };
+template <> struct Cfg<float2> {
+  static constexpr int NT = 512, NW = 1, TILE = 8192, MINB = LSP_MINB_C64;
+};
+template <> struct Cfg<double2> {
+  static constexpr int NT = 256, NW = 1, TILE = 4096, MINB = LSP_MINB_C128;
+};
 
 // Line lengths of a 2^M-point lattice: N2 = 2^min(10, M/2) (column), N1 = n / N2 (row).
 template <int M> struct Split {
@@ -72,22 +77,22 @@ template <int M> struct Split {
   static constexpr int LN1 = M - LN2;
 };
 
-template <typename T, int M> using RowLine = Line<T, Cfg<T>::NT, Split<M>::LN1, true>;
-template <typename T, int M> using ColLine = Line<T, Cfg<T>::NT, Split<M>::LN2, false>;
+template <typename T, int M> using RowLine = Line<T, Cfg<T>::NT, Split<M>::LN1, true, Cfg<T>::NW>;
+template <typename T, int M> using ColLine = Line<T, Cfg<T>::NT, Split<M>::LN2, false, Cfg<T>::NW>;
 
 // Shared memory of the persistent kernel: exchange buffer, prefetch buffer
 // and (when everything fits in 227 KiB) the twiddle tables.
 template <typename T, int M> struct SmemLayout {
-  static constexpr int TILE = Cfg<T>::TILE;
-  static constexpr int work = 0;
-  static constexpr int pre = TILE;
-  static constexpr int twr = 2 * TILE;
+  static constexpr int TILE = Cfg<T>::TILE, NW = Cfg<T>::NW;
+  static constexpr int work(int w) { return 2 * TILE * w; }
+  static constexpr int pre(int w) { return 2 * TILE * w + TILE; }
+  static constexpr int twr = 2 * TILE * NW;
   static constexpr int twc = twr + RowLine<T, M>::TW_ENTRIES;
   static constexpr int twl = twc + ColLine<T, M>::TW_ENTRIES;
   static constexpr int twf = twl + (1 << Split<M>::LN1);
   static constexpr int elems_all = twf + (1 << Split<M>::LN2);
   static constexpr bool tw_in_smem = (size_t)elems_all * sizeof(T) <= 227u * 1024u - 256u;
-  static constexpr size_t bytes = (size_t)(tw_in_smem ? elems_all : 2 * TILE) * sizeof(T);
+  static constexpr size_t bytes = (size_t)(tw_in_smem ? elems_all : twr) * sizeof(T);
 };
 
 // ---------------------------------------------------------------------------
@@ -152,10 +157,11 @@ __device__ __forceinline__ void prefetch_tile(const MPInst<T>& I, int tile, T* p
 // i * C + b); after reading it the pass refills the buffer with tile `nxt`.
 // ---------------------------------------------------------------------------
 template <typename T, int NT, int M, int KIND, int FROM>
-__device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T* pre, Tw<T> tw, int nxt = -1,
+__device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T* pre, Tw<T> tw,
+                                         const MPInst<T>* In = nullptr, int nxt = -1,
                                          unsigned long long* mb = nullptr) {
   constexpr int LOGL = Split<M>::LN2, lN1 = Split<M>::LN1;
-  using G = Line<T, NT, LOGL, false>;
+  using G = Line<T, NT, LOGL, false, Cfg<T>::NW>;
   constexpr int LR1 = G::LOGR1, R1 = G::R1;
   constexpr bool inv = (KIND == kMid || KIND == kTail);
   constexpr bool fwd = (KIND == kHead || KIND == kMid || KIND == kColFwd);
@@ -185,8 +191,8 @@ __device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T*
     }
   }
   if constexpr (FROM == kFromPre) {
-    __syncthreads();                                     // prefetch buffer free: refill it
-    if (nxt >= 0) { fence_proxy_async(); prefetch_tile<T, NT, M, true>(I, nxt, pre, mb); }
+    G::sync();                                           // prefetch buffer free: refill it
+    if (nxt >= 0) { fence_proxy_async(); prefetch_tile<T, NT, M, true>(*In, nxt, pre, mb); }
   }
   if constexpr (inv) G::idft(sm, tw.line, v);
 
@@ -230,10 +236,11 @@ __device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T*
 // sits in the prefetch buffer row-major (b * L + i).
 // ---------------------------------------------------------------------------
 template <typename T, int NT, int M, int KIND, int FROM>
-__device__ __forceinline__ void row_pass(const MPInst<T>& I, int tile, T* sm, T* pre, Tw<T> tw, int nxt = -1,
+__device__ __forceinline__ void row_pass(const MPInst<T>& I, int tile, T* sm, T* pre, Tw<T> tw,
+                                         const MPInst<T>* In = nullptr, int nxt = -1,
                                          unsigned long long* mb = nullptr) {
   constexpr int LOGL = Split<M>::LN1, lN2 = Split<M>::LN2;
-  using G = Line<T, NT, LOGL, true>;
+  using G = Line<T, NT, LOGL, true, Cfg<T>::NW>;
   constexpr int LR1 = G::LOGR1, R1 = G::R1;
   const int r0 = tile << G::LOGC;
   T* __restrict__ u = I.u;
@@ -249,8 +256,8 @@ __device__ __forceinline__ void row_pass(const MPInst<T>& I, int tile, T* sm, T*
     }
   }
   if constexpr (FROM == kFromPre) {
-    __syncthreads();
-    if (nxt >= 0) { fence_proxy_async(); prefetch_tile<T, NT, M, false>(I, nxt, pre, mb); }
+    G::sync();
+    if (nxt >= 0) { fence_proxy_async(); prefetch_tile<T, NT, M, false>(*In, nxt, pre, mb); }
   }
 
   G::dft(sm, tw.line, v);
@@ -309,23 +316,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& target, in
   return s_ok != 0;
 }
 
+// Sweep tile t -> (instance, local tile); a null map means a single instance.
+template <typename T>
+__device__ __forceinline__ void tile_of(const int2* map, int t, int& inst, int& local) {
+  if (map) { const int2 m = map[t]; inst = m.x; local = m.y; }
+  else { inst = 0; local = t; }
+}
+
 // Issue the bulk copies of one tile into the prefetch buffer (all threads).
 template <typename T, int NT, int M, bool COL>
 __device__ __forceinline__ void prefetch_tile(const MPInst<T>& I, int tile, T* pre, unsigned long long* mb) {
   constexpr int TILE = Cfg<T>::TILE;
   if constexpr (COL) {
     constexpr int LOGL = Split<M>::LN2, lN1 = Split<M>::LN1;
-    constexpr int LOGC = Line<T, NT, LOGL, false>::LOGC;
+    using G = Line<T, NT, LOGL, false, Cfg<T>::NW>;
+    constexpr int LOGC = G::LOGC;
     constexpr int L = 1 << LOGL, C = 1 << LOGC;
     const T* src = I.u + (tile << LOGC);
-    for (int i = threadIdx.x; i < L; i += NT)
+    for (int i = G::tid(); i < L; i += NT)
       bulk_g2s(pre + i * C, src + ((size_t)i << lN1), C * (unsigned)sizeof(T), mb);
   } else {
     constexpr int CHUNK = 4096 / (int)sizeof(T);   // 4 KiB per copy
     constexpr int LOGL = Split<M>::LN1;
-    constexpr int LOGC = Line<T, NT, LOGL, true>::LOGC;
+    using G = Line<T, NT, LOGL, true, Cfg<T>::NW>;
+    constexpr int LOGC = G::LOGC;
     const T* src = I.u + ((size_t)tile << (LOGL + LOGC));
-    for (int c = threadIdx.x; c < TILE / CHUNK; c += NT)
+    for (int c = G::tid(); c < TILE / CHUNK; c += NT)
       bulk_g2s(pre + c * CHUNK, src + c * CHUNK, CHUNK * (unsigned)sizeof(T), mb);
   }
 }
@@ -344,76 +360,101 @@ __device__ __forceinline__ bool wait_prefetch(unsigned long long* mb, unsigned p
   return true;
 }
 
-// One sweep inside the persistent kernel: every tile of this CTA, the copy of
-// the next tile in flight while the current one is transformed.
+// One sweep inside the persistent kernel for this thread's worker: every
+// tile of the worker, the copy of the next tile in flight while the current
+// one is transformed.  Returns false (uniformly per worker) if a bounded wait
+// expired.
 template <typename T, int NT, int M, bool COL>
 __device__ __forceinline__ bool persistent_sweep(const MPParams<T>& P, T* smem, Tw<T> tw,
-                                                 unsigned long long* mb, unsigned& parity) {
+                                                 unsigned long long* mb, unsigned& parity, int* fail) {
   using SL = SmemLayout<T, M>;
+  using G = Line<T, NT, COL ? Split<M>::LN2 : Split<M>::LN1, !COL, Cfg<T>::NW>;
+  constexpr int NW = Cfg<T>::NW;
   constexpr unsigned TILE_BYTES = Cfg<T>::TILE * (unsigned)sizeof(T);
-  T* sm = smem + SL::work;
-  T* pre = smem + SL::pre;
-  const MPInst<T>& I = P.inst[0];
+  const int w = NW == 1 ? 0 : (int)(threadIdx.x / NT);
+  T* sm = smem + SL::work(w);
+  T* pre = smem + SL::pre(w);
+  const int2* map = COL ? P.colmap : P.rowmap;
   const int total = COL ? P.total_col : P.total_row;
-  int t = blockIdx.x;
+  const int stride = (int)gridDim.x * NW;
+  int t = (int)blockIdx.x * NW + w;
   if (t >= total) return true;
-  if (threadIdx.x == 0) mbar_arrive_expect_tx(mb, TILE_BYTES);
-  __syncthreads();
+  int i, l;
+  tile_of<T>(map, t, i, l);
+  if (G::tid() == 0) mbar_arrive_expect_tx(mb, TILE_BYTES);
+  G::sync();
   fence_proxy_async();
-  prefetch_tile<T, NT, M, COL>(I, t, pre, mb);
-  for (; t < total; t += gridDim.x) {
-    if (!wait_prefetch(mb, parity, P.err)) return false;
+  prefetch_tile<T, NT, M, COL>(P.inst[i], l, pre, mb);
+  for (; t < total; t += stride) {
+    if (!wait_prefetch(mb, parity, P.err)) fail[w] = 1;
+    G::sync();
+    if (fail[w]) return false;
     parity ^= 1u;
-    const int nxt = t + (int)gridDim.x < total ? t + (int)gridDim.x : -1;
-    if (threadIdx.x == 0 && nxt >= 0) mbar_arrive_expect_tx(mb, TILE_BYTES);
-    if constexpr (COL) col_pass<T, NT, M, kMid, kFromPre>(I, t, sm, pre, tw, nxt, mb);
-    else row_pass<T, NT, M, kRow, kFromPre>(I, t, sm, pre, tw, nxt, mb);
+    int in = 0, ln = -1;
+    if (t + stride < total) tile_of<T>(map, t + stride, in, ln);
+    if (G::tid() == 0 && ln >= 0) mbar_arrive_expect_tx(mb, TILE_BYTES);
+    if constexpr (COL) col_pass<T, NT, M, kMid, kFromPre>(P.inst[i], l, sm, pre, tw, &P.inst[in], ln, mb);
+    else row_pass<T, NT, M, kRow, kFromPre>(P.inst[i], l, sm, pre, tw, &P.inst[in], ln, mb);
+    i = in;
+    l = ln;
   }
   return true;
 }
 
 // Sweeps 1..2N-1 of N steps, after a head sweep: row, mid, row, ..., mid, row;
-// a bounded grid barrier separates consecutive sweeps.
+// a bounded grid barrier separates consecutive sweeps.  A worker whose wait
+// expired skips to the barrier, where the error word stops every CTA.
 template <typename T, int NT, int M>
-__global__ void __launch_bounds__(NT, Cfg<T>::MINB) mp_persistent(const __grid_constant__ MPParams<T> P) {
+__global__ void __launch_bounds__(NT * Cfg<T>::NW, Cfg<T>::MINB) mp_persistent(const __grid_constant__ MPParams<T> P) {
   using SL = SmemLayout<T, M>;
+  constexpr int NW = Cfg<T>::NW;
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) unsigned long long mb;
+  __shared__ __align__(8) unsigned long long mb[NW];
+  __shared__ int fail[NW];
   T* smem = reinterpret_cast<T*>(smraw);
   const MPInst<T>& I = P.inst[0];
   Tw<T> twr{I.twr, I.twl, I.twf}, twc{I.twc, I.twl, I.twf};
+  constexpr int CT = NT * NW;
   if constexpr (SL::tw_in_smem) {
-    for (int k = threadIdx.x; k < RowLine<T, M>::TW_ENTRIES; k += NT) smem[SL::twr + k] = I.twr[k];
-    for (int k = threadIdx.x; k < ColLine<T, M>::TW_ENTRIES; k += NT) smem[SL::twc + k] = I.twc[k];
-    for (int k = threadIdx.x; k < (1 << Split<M>::LN1); k += NT) smem[SL::twl + k] = I.twl[k];
-    for (int k = threadIdx.x; k < (1 << Split<M>::LN2); k += NT) smem[SL::twf + k] = I.twf[k];
+    for (int k = threadIdx.x; k < RowLine<T, M>::TW_ENTRIES; k += CT) smem[SL::twr + k] = I.twr[k];
+    for (int k = threadIdx.x; k < ColLine<T, M>::TW_ENTRIES; k += CT) smem[SL::twc + k] = I.twc[k];
+    for (int k = threadIdx.x; k < (1 << Split<M>::LN1); k += CT) smem[SL::twl + k] = I.twl[k];
+    for (int k = threadIdx.x; k < (1 << Split<M>::LN2); k += CT) smem[SL::twf + k] = I.twf[k];
     twr = Tw<T>{smem + SL::twr, smem + SL::twl, smem + SL::twf};
     twc = Tw<T>{smem + SL::twc, smem + SL::twl, smem + SL::twf};
   }
-  if (threadIdx.x == 0) mbar_init(&mb, 1);
+  if (threadIdx.x < NW) {
+    mbar_init(&mb[threadIdx.x], 1);
+    fail[threadIdx.x] = 0;
+  }
   __syncthreads();
+  const int w = NW == 1 ? 0 : (int)(threadIdx.x / NT);
   unsigned target = 0, parity = 0;
   for (long long step = 0; step < P.nsteps; ++step) {
-    if (!persistent_sweep<T, NT, M, false>(P, smem, twr, &mb, parity)) return;
+    persistent_sweep<T, NT, M, false>(P, smem, twr, &mb[w], parity, fail);
     if (step + 1 == P.nsteps) break;
     if (!grid_barrier(P.bar, target, P.err)) return;
-    if (!persistent_sweep<T, NT, M, true>(P, smem, twc, &mb, parity)) return;
+    persistent_sweep<T, NT, M, true>(P, smem, twc, &mb[w], parity, fail);
     if (!grid_barrier(P.bar, target, P.err)) return;
   }
 }
 
 // One sweep of kind KIND per launch (head and tail sweeps, spectral output),
-// reading the tile and the twiddle tables from global memory.
+// reading the tiles and the twiddle tables from global memory.
 template <typename T, int NT, int M, int KIND>
-__global__ void __launch_bounds__(NT, Cfg<T>::MINB) mp_sweep(const __grid_constant__ MPParams<T> P) {
+__global__ void __launch_bounds__(NT * Cfg<T>::NW, Cfg<T>::MINB) mp_sweep(const __grid_constant__ MPParams<T> P) {
+  constexpr int NW = Cfg<T>::NW;
   extern __shared__ __align__(128) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
+  const int w = NW == 1 ? 0 : (int)(threadIdx.x / NT);
+  T* sm = reinterpret_cast<T*>(smraw) + w * Cfg<T>::TILE;
   constexpr bool col = KIND != kRow && KIND != kRowFwd;
   const int total = col ? P.total_col : P.total_row;
-  const MPInst<T>& I = P.inst[0];
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    if constexpr (col) col_pass<T, NT, M, KIND, kFromGlobal>(I, t, sm, nullptr, Tw<T>{I.twc, I.twl, I.twf});
-    else row_pass<T, NT, M, KIND, kFromGlobal>(I, t, sm, nullptr, Tw<T>{I.twr, I.twl, I.twf});
+  for (int t = (int)blockIdx.x * NW + w; t < total; t += (int)gridDim.x * NW) {
+    int i, l;
+    tile_of<T>(col ? P.colmap : P.rowmap, t, i, l);
+    const MPInst<T>& I = P.inst[i];
+    if constexpr (col) col_pass<T, NT, M, KIND, kFromGlobal>(I, l, sm, nullptr, Tw<T>{I.twc, I.twl, I.twf});
+    else row_pass<T, NT, M, KIND, kFromGlobal>(I, l, sm, nullptr, Tw<T>{I.twr, I.twl, I.twf});
   }
 }
 

@@ -1,5 +1,7 @@
 // Host side of the multipass Strang step: kernel selection per lattice size,
 // descriptors, cooperative persistent launches and single-sweep launches.
+#include <string.h>
+
 #include <algorithm>
 
 #include "lsp_mp.cuh"
@@ -43,7 +45,7 @@ static MPInst<T> make_inst(lsp_plan pl, double2* spec) {
 
 // Co-resident CTA count of a kernel (cached per kernel pointer).
 template <typename T> static int coresident(const void* fn, size_t smem, int& grid) {
-  constexpr int NT = Cfg<T>::NT;
+  constexpr int NT = Cfg<T>::NT * Cfg<T>::NW;
   static const void* cfn[64] = {};
   static int cval[64] = {};
   for (int i = 0; i < 64; ++i)
@@ -64,12 +66,12 @@ int launch_persistent(int m, const MPInst<T>* dinst, const int2* colmap, const i
                       int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
   MPKernels k;
   if (!kernels_for(sizeof(T) == 8 ? LSP_C64 : LSP_C128, m, &k)) return LSP_ERR_TOO_LARGE;
-  constexpr int NT = Cfg<T>::NT;
+  constexpr int NT = Cfg<T>::NT * Cfg<T>::NW;
   const size_t smem = k.persistent_smem;
   int grid = 0;
   int rc = coresident<T>(k.persistent, smem, grid);
   if (rc) return rc;
-  grid = std::min(grid, std::max(total_col, total_row));
+  grid = std::min(grid, (std::max(total_col, total_row) + Cfg<T>::NW - 1) / Cfg<T>::NW);
   MPParams<T> P{dinst, colmap, rowmap, ninst, total_col, total_row, (long long)nsteps, 0, bar, err};
   LSP_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
   void* args[] = {&P};
@@ -82,13 +84,13 @@ int launch_sweep(int m, const MPInst<T>* dinst, const int2* colmap, const int2* 
                  int total_col, int total_row, int kind, cudaStream_t s) {
   MPKernels k;
   if (!kernels_for(sizeof(T) == 8 ? LSP_C64 : LSP_C128, m, &k)) return LSP_ERR_TOO_LARGE;
-  constexpr int NT = Cfg<T>::NT;
-  const size_t smem = (size_t)Cfg<T>::TILE * sizeof(T);
+  constexpr int NT = Cfg<T>::NT * Cfg<T>::NW;
+  const size_t smem = (size_t)Cfg<T>::TILE * Cfg<T>::NW * sizeof(T);
   int grid = 0;
   int rc = coresident<T>(k.sweep[kind], smem, grid);
   if (rc) return rc;
   const bool col = kind != kRow && kind != kRowFwd;
-  grid = std::min(grid, col ? total_col : total_row);
+  grid = std::min(grid, ((col ? total_col : total_row) + Cfg<T>::NW - 1) / Cfg<T>::NW);
   MPParams<T> P{dinst, colmap, rowmap, ninst, total_col, total_row, 0, kind, nullptr, nullptr};
   void* args[] = {&P};
   LSP_CUDA_TRY(cudaLaunchKernel(k.sweep[kind], dim3(grid), dim3(NT), args, smem, s));
@@ -148,6 +150,38 @@ int multipass_steps(lsp_plan p, int64_t nsteps, cudaStream_t s) {
 
 int multipass_spectral(lsp_plan p, cudaStream_t s) {
   return p->prec == LSP_C64 ? spectral_impl<float2>(p, s) : spectral_impl<double2>(p, s);
+}
+
+// Batching: descriptors of many same-size plans in one device array; the tile
+// maps enumerate (instance, local tile) over all of them.
+int multipass_desc_size(int prec) { return multipass_desc_bytes(prec); }
+
+void multipass_fill_desc(lsp_plan p, void* host_out, int* ncol, int* nrow) {
+  if (p->prec == LSP_C64) {
+    MPInst<float2> I = make_inst<float2>(p, nullptr);
+    memcpy(host_out, &I, sizeof(I));
+    *ncol = I.ncol; *nrow = I.nrow;
+  } else {
+    MPInst<double2> I = make_inst<double2>(p, nullptr);
+    memcpy(host_out, &I, sizeof(I));
+    *ncol = I.ncol; *nrow = I.nrow;
+  }
+}
+
+template <typename T>
+static int batch_impl(int m, const void* ddesc, const int2* colmap, const int2* rowmap, int ninst, int total_col,
+                      int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
+  const MPInst<T>* d = (const MPInst<T>*)ddesc;
+  int rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kHead, s);
+  if (!rc) rc = launch_persistent<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
+  if (!rc) rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kTail, s);
+  return rc;
+}
+
+int multipass_batch_steps(int prec, int m, const void* ddesc, const int2* colmap, const int2* rowmap, int ninst,
+                          int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
+  return prec == LSP_C64 ? batch_impl<float2>(m, ddesc, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s)
+                         : batch_impl<double2>(m, ddesc, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
 }
 
 }  // namespace lsp

@@ -9,6 +9,8 @@
 // with s = (o / Ns) mod R and j = (o / (Ns R)) Ns + o mod Ns.
 // One step follows Algorithm 1 in physical form with merged half steps:
 //   u <- P . F^{-1} K F u   (P_half before the first and after the last step).
+#include <string.h>
+
 #include <algorithm>
 
 #include "lsp_internal.cuh"
@@ -180,6 +182,24 @@ int small_steps(lsp_plan p, int64_t nsteps, cudaStream_t s) {
 int small_spectral(lsp_plan p, cudaStream_t s) {
   return p->prec == LSP_C64 ? small_launch<float2>(p->desc, 1, (int)p->ntot, 0, 1, s)
                             : small_launch<double2>(p->desc, 1, (int)p->ntot, 0, 1, s);
+}
+
+// Batching: descriptors of many plans in one device array, one CTA per instance.
+int small_desc_size(int prec) { return small_desc_bytes(prec); }
+
+void small_fill_desc(lsp_plan p, void* host_out) {
+  if (p->prec == LSP_C64) {
+    SmallDesc<float2> S = make_small<float2>(p);
+    memcpy(host_out, &S, sizeof(S));
+  } else {
+    SmallDesc<double2> S = make_small<double2>(p);
+    memcpy(host_out, &S, sizeof(S));
+  }
+}
+
+int small_batch_launch(int prec, const void* ddesc, int count, int max_n, int64_t nsteps, cudaStream_t s) {
+  return prec == LSP_C64 ? small_launch<float2>(ddesc, count, max_n, nsteps, 0, s)
+                         : small_launch<double2>(ddesc, count, max_n, nsteps, 0, s);
 }
 
 }  // namespace lsp

@@ -140,9 +140,19 @@ template <> struct Swz<double2> {  // 8 x 16 B per 128 B bank row
 // ---------------------------------------------------------------------------
 // Compile-time line geometry
 // ---------------------------------------------------------------------------
-template <typename T, int NT, int LOGL, bool MAJOR>
+// NW independent workers of NT threads share a CTA; each transforms its own
+// tile and synchronises on its own named barrier (id 1 + worker).
+template <typename T, int NT, int LOGL, bool MAJOR, int NW = 1>
 struct Line {
   static constexpr int L = 1 << LOGL;
+  static __device__ __forceinline__ int tid() { return NW == 1 ? (int)threadIdx.x : (int)(threadIdx.x & (NT - 1)); }
+  static __device__ __forceinline__ void sync() {
+    if constexpr (NW == 1) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / NT)), "r"(NT) : "memory");
+    }
+  }
   static constexpr int LOGNT = NT == 512 ? 9 : NT == 256 ? 8 : NT == 128 ? 7 : 10;
   static constexpr int LOGC = LOGNT + 4 - LOGL;      // lines per tile
   static constexpr int C = 1 << LOGC;
@@ -168,7 +178,7 @@ struct Line {
   // q-th butterfly of this thread for radix 2^LR -> (line b, butterfly j)
   template <int LR>
   static __device__ __forceinline__ void bm(int q, int& b, int& j) {
-    const int beta = threadIdx.x + NT * q;
+    const int beta = tid() + NT * q;
     if constexpr (MAJOR) { j = beta & ((1 << (LOGL - LR)) - 1); b = beta >> (LOGL - LR); }
     else { b = beta & (C - 1); j = beta >> LOGC; }
   }
@@ -260,12 +270,12 @@ struct Line {
   template <int S = 1>
   static __device__ __forceinline__ void dft(T* sm, const T* tw, T (&v)[16]) {
     if constexpr (S > 1) {
-      __syncthreads();
+      sync();
       read_in<S>(sm, v);
     }
     fwd_body<S>(tw, v);
     if constexpr (S < P) {
-      __syncthreads();
+      sync();
       write_out<S>(sm, v);
       dft<S + 1>(sm, tw, v);
     } else {
@@ -284,12 +294,12 @@ struct Line {
   template <int S = P>
   static __device__ __forceinline__ void idft(T* sm, const T* tw, T (&v)[16]) {
     if constexpr (S < P) {
-      __syncthreads();
+      sync();
       read_out<S>(sm, v);
     }
     inv_body<S>(tw, v);
     if constexpr (S > 1) {
-      __syncthreads();
+      sync();
       write_in<S>(sm, v);
       idft<S - 1>(sm, tw, v);
     }

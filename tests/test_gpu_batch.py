@@ -1,0 +1,76 @@
+"""Batched stepping (lsp_batch_*) against the oracle and against single-plan runs (GB300)."""
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+from oracle import strang as S
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "c64": 5e-5}
+
+
+def _setup(lib, insts, prec):
+    import torch
+    plans, ref_in = [], []
+    for inst in insts:
+        P = L.lattice_points(inst.Z, inst.n)
+        v, u0 = inst.v(P), inst.u0(P)
+        p = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec)
+        p.set_potential(torch.from_numpy(v).cuda())
+        p.set_state(torch.from_numpy(u0).cuda())
+        plans.append(p)
+        ref_in.append((v, u0))
+    return plans, ref_in
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_batch_matches_oracle_and_single_runs(lib, prec):
+    insts = w.c3(count=12, seed=7, min_log2=12, max_log2=16)
+    nsteps = 30
+    plans, ref_in = _setup(lib, insts, prec)
+    paths = {p.info()["path"] for p in plans}
+    assert paths == {lib.PATH_SMALL, lib.PATH_MULTIPASS}        # both groups exercised
+    batch = lib.Batch(plans)
+    batch.steps([inst.dt for inst in insts], nsteps)
+    assert batch.status() == 0
+    got = [p.get_state(prec="c128").cpu().numpy() for p in plans]
+    # same instances run singly
+    singles, _ = _setup(lib, insts, prec)
+    for p, inst in zip(singles, insts):
+        p.strang_steps(inst.dt, nsteps)
+    for g, p, inst, (v, u0) in zip(got, singles, insts, ref_in):
+        s = p.get_state(prec="c128").cpu().numpy()
+        assert np.array_equal(g, s), inst.name
+        norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+        ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, nsteps)
+        err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert err < TOL[prec], (inst.name, err)
+    batch.destroy()
+
+
+def test_batch_repeated_calls_and_zero_steps(lib):
+    insts = w.c3(count=5, seed=3, min_log2=13, max_log2=15)
+    plans, ref_in = _setup(lib, insts, "c64")
+    batch = lib.Batch(plans)
+    dts = [inst.dt for inst in insts]
+    batch.steps(dts, 0)
+    batch.steps(dts, 7)
+    batch.steps(dts, 8)
+    assert batch.status() == 0
+    for p, inst, (v, u0) in zip(plans, insts, ref_in):
+        norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+        ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 15)
+        g = p.get_state(prec="c128").cpu().numpy()
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < TOL["c64"]
+
+
+def test_batch_rejects_mixed_precision(lib):
+    insts = w.c3(count=2, seed=1, min_log2=12, max_log2=13)
+    a = lib.Plan(insts[0].Zmat, insts[0].n, 0.1, prec="c64")
+    b = lib.Plan(insts[1].Zmat, insts[1].n, 0.1, prec="c128")
+    with pytest.raises(lib.LspError) as e:
+        lib.Batch([a, b])
+    assert e.value.code == -8
