@@ -108,11 +108,24 @@ def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def _buf(x):
-    """(pointer, on_device) for a torch tensor or numpy array."""
+_KEEP = threading.local()
+
+
+def _buf(x, output: bool = False):
+    """(pointer, on_device) for a torch tensor or numpy array.
+
+    Torch views with a lazy conjugate or negative bit do not hold the values
+    they represent in memory: inputs are materialised (the copy is kept alive
+    until the next call from this thread, and is stream-ordered anyway);
+    outputs must be plain tensors."""
     try:
         import torch
         if isinstance(x, torch.Tensor):
+            if x.is_complex() and (x.is_conj() or x.is_neg()):
+                if output:
+                    raise ValueError("output tensor must not be a conjugate or negative view")
+                x = x.resolve_conj().resolve_neg()
+                _KEEP.t = x
             if not x.is_contiguous():
                 raise ValueError("tensor must be contiguous")
             return C.c_void_p(x.data_ptr()), int(x.is_cuda)
@@ -196,7 +209,7 @@ class Plan:
             out = torch.empty(self.npoints, dtype=torch.complex64 if pc == C64 else torch.complex128,
                               device=f"cuda:{self.device}")
         pc = C64 if str(out.dtype).endswith("complex64") else C128
-        ptr, dev = _buf(out)
+        ptr, dev = _buf(out, output=True)
         _check(self._lib.lsp_get_state(self._h, ptr, pc, sp, dev, _stream_ptr(stream)), "lsp_get_state")
         return out
 
@@ -262,7 +275,7 @@ def strang_steps_noalloc(u, v, norm2, gamma: float, dt: float, nsteps: int, stre
     (u complex64/complex128 updated in place, v float64, norm2 int32)."""
     lib = load_library()
     prec = C64 if str(u.dtype).endswith("complex64") else C128
-    up, _ = _buf(u)
+    up, _ = _buf(u, output=True)
     vp, _ = _buf(v)
     np_, _ = _buf(norm2)
     _check(lib.lsp_strang_steps_noalloc(prec, int(u.numel()), float(gamma), float(dt), int(nsteps), vp, np_, up,
@@ -272,7 +285,7 @@ def strang_steps_noalloc(u, v, norm2, gamma: float, dt: float, nsteps: int, stre
 def adjoint(plan: Plan, dt: float, nsteps: int, lamT, grad_v, grad_u0, ckpt_stride: int = 0, stream=None):
     """lsp_adjoint: gradients of a real objective of u_T w.r.t. v and u_0 (device tensors)."""
     lp, _ = _buf(lamT)
-    gv, _ = _buf(grad_v)
-    gu, _ = _buf(grad_u0)
+    gv, _ = _buf(grad_v, output=True)
+    gu, _ = _buf(grad_u0, output=True)
     _check(plan._lib.lsp_adjoint(plan.handle, float(dt), int(nsteps), lp, gv, gu, int(ckpt_stride),
                                  _stream_ptr(stream)), "lsp_adjoint")

@@ -625,10 +625,5 @@ int lsp_plan_info(lsp_plan p, int64_t* info) {
   return LSP_OK;
 }
 
-int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double* grad_v, void* grad_u0,
-                int64_t ckpt_stride, void* stream) {
-  (void)p; (void)dt; (void)nsteps; (void)lamT; (void)grad_v; (void)grad_u0; (void)ckpt_stride; (void)stream;
-  return LSP_ERR_UNSUPPORTED;
-}
 
 }  // extern "C"

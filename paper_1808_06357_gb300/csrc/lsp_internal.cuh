@@ -200,6 +200,9 @@ int multipass_spectral(lsp_plan p, cudaStream_t s);       // -> p->stage (chi or
 int small_steps(lsp_plan p, int64_t nsteps, cudaStream_t s);
 int small_spectral(lsp_plan p, cudaStream_t s);           // -> p->stage (chi order, c128)
 int build_phase_tables(lsp_plan p, double dt, cudaStream_t s);
+// steps of the plan's kernels on another state buffer of the same geometry
+int multipass_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
+int small_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 // batching hooks: descriptor bytes of a plan, and launches over descriptor arrays
 int small_desc_size(int prec);
 void small_fill_desc(lsp_plan p, void* host_out);

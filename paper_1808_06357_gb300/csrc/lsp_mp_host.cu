@@ -130,6 +130,25 @@ static int steps_impl(lsp_plan p, int64_t nsteps, cudaStream_t s) {
   return rc;
 }
 
+// Steps on another state buffer of the plan's geometry (descriptor slot 2),
+// with the plan's current phase tables.
+template <typename T>
+static int steps_on_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  MPInst<T> I = make_inst<T>(p, nullptr);
+  I.u = (T*)state;
+  MPInst<T>* d = (MPInst<T>*)p->desc + 2;
+  LSP_CUDA_TRY(cudaMemcpyAsync(d, &I, sizeof(I), cudaMemcpyHostToDevice, s));
+  int rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kHead, s);
+  if (!rc) rc = launch_persistent<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
+  if (!rc) rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kTail, s);
+  return rc;
+}
+
+int multipass_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  return p->prec == LSP_C64 ? steps_on_impl<float2>(p, state, nsteps, s)
+                            : steps_on_impl<double2>(p, state, nsteps, s);
+}
+
 // Spectral coefficients (eq. approx_uhat) of the current state into the
 // plan's staging buffer in chi order: column DFT + twiddle, then row DFT / n,
 // on a copy of the state.

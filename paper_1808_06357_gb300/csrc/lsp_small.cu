@@ -184,6 +184,21 @@ int small_spectral(lsp_plan p, cudaStream_t s) {
                             : small_launch<double2>(p->desc, 1, (int)p->ntot, 0, 1, s);
 }
 
+// Steps on another state buffer of the plan's geometry (descriptor slot 1),
+// with the plan's current phase tables.
+template <typename T> static int small_steps_on_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  SmallDesc<T> S = make_small<T>(p);
+  S.u = (T*)state;
+  SmallDesc<T>* d = (SmallDesc<T>*)p->desc + 1;
+  LSP_CUDA_TRY(cudaMemcpyAsync(d, &S, sizeof(S), cudaMemcpyHostToDevice, s));
+  return small_launch<T>(d, 1, (int)p->ntot, nsteps, 0, s);
+}
+
+int small_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  return p->prec == LSP_C64 ? small_steps_on_impl<float2>(p, state, nsteps, s)
+                            : small_steps_on_impl<double2>(p, state, nsteps, s);
+}
+
 // Batching: descriptors of many plans in one device array, one CTA per instance.
 int small_desc_size(int prec) { return small_desc_bytes(prec); }
 

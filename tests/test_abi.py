@@ -47,3 +47,20 @@ def test_plan_create_fails_loudly_without_gpu():
     with pytest.raises(lsp.LspError) as e:
         lsp.Plan(np.array([1, 5]), (64,), 0.1)
     assert e.value.code == -6
+
+
+def test_binding_resolves_conjugate_views():
+    """A lazily conjugated torch view is materialised before its pointer is passed; as an
+    output it is refused (its memory does not hold the values it represents)."""
+    import numpy as np
+    import pytest
+    import torch
+    from paper_1808_06357_gb300 import _binding as B
+    x = torch.tensor([1 + 2j, 3 - 4j], dtype=torch.complex128)
+    cx = torch.conj(x)
+    assert cx.is_conj()
+    ptr, dev = B._buf(cx)
+    got = np.ctypeslib.as_array((ctypes.c_double * 4).from_address(ptr.value))
+    assert np.array_equal(got, [1.0, -2.0, 3.0, 4.0]) and dev == 0
+    with pytest.raises(ValueError):
+        B._buf(cx, output=True)
