@@ -45,8 +45,8 @@ typedef struct lsp_batch_s* lsp_batch;
 enum {
   LSP_OK = 0,
   LSP_ERR_BAD_ARG = -1,        /* invalid argument (null pointer, size, mode)                  */
-  LSP_ERR_NOT_CANONICAL = -2,  /* lattice violates Def. 1 (n_{i+1} | n_i, gcd(z_i, n_i) = 1,
-                                  n distinct points)                                         */
+  LSP_ERR_NOT_CANONICAL = -2,  /* lattice not in canonical form as read from Def. 1:
+                                  n_{i+1} | n_i and n = prod n_i distinct points             */
   LSP_ERR_NOT_INJECTIVE = -3,  /* explicit index set violates Def. 2 or has |A| != n         */
   LSP_ERR_TOO_LARGE = -4,      /* size beyond what the kernels support                       */
   LSP_ERR_OOM = -5,            /* device allocation failed                                   */
@@ -86,6 +86,12 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * Errors: BAD_ARG, NOT_CANONICAL, NOT_INJECTIVE, TOO_LARGE, OOM, CUDA,
  * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
  * The state starts at zero and the potential at v = 0.
+ * Execution paths (chosen here, reported by lsp_plan_info):
+ *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
+ *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, rank 1 or 2;
+ *   2 multipass, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
+ *     (10, 8), (11, 9), (12, 10), (14, 12).
+ * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
                     const int32_t* index_set, int64_t m, int aa_mode, int prec,
@@ -158,16 +164,18 @@ int lsp_index_table(lsp_plan p, int32_t* h);
 /*
  * lsp_plan_info -- plan geometry, 8 int64 values (host):
  *   [0] n  [1] N1 (row length)  [2] N2 (column length)  [3] path (0 multipass,
- *   1 SMEM-resident)  [4] precision  [5] device bytes held  [6] MINL2 DP box
- *   half-width (0 for EXPLICIT)  [7] max ||h_chi||^2.
+ *   1 SMEM-resident, 2 rank-2 multipass)  [4] precision  [5] device bytes held
+ *   [6] MINL2 DP box half-width (0 for EXPLICIT)  [7] max ||h_chi||^2.
+ *   For rank 2, N1 = n_2 (contiguous rows) and N2 = n_1.
  */
 int lsp_plan_info(lsp_plan p, int64_t* info);
 
 /*
  * Batched stepping: many independent instances (same precision and device)
  * advanced together.  Instances on the SMEM-resident path share one launch
- * (one CTA each); multipass instances are grouped by lattice size, one
- * persistent cooperative launch per size per call.
+ * (one CTA each); rank-1 multipass instances are grouped by lattice size, one
+ * persistent cooperative launch per size per call; rank-2 multipass instances
+ * (each large enough to fill the device) are stepped one after another.
  *   lsp_batch_create  plans: `count` plan handles (host array, borrowed: the
  *                     plans must outlive the batch).  Errors: BAD_ARG, OOM, CUDA,
  *                     UNSUPPORTED (mixed precision or device).

@@ -85,6 +85,60 @@ def strang(u0: np.ndarray, v: np.ndarray, norms2: np.ndarray, n, gamma: float,
 
 
 # --------------------------------------------------------------------------
+# Values computed one at a time (spot checks on lattices too large for the
+# full oracle run)
+# --------------------------------------------------------------------------
+def coeff_at(u: np.ndarray, n, xi: np.ndarray) -> np.ndarray:
+    """uhat at the bins xi (rows (xi_1, ..., xi_r)) by the direct sum of eq. approx_uhat.
+
+    With p_k = sum_i z_i k_i / n_i, h . p_k = sum_i xi_i k_i / n_i mod 1
+    (xi_i = h . z_i mod n_i), so uhat(xi) = (1/N) sum_k u_k exp(-2 pi i sum_i xi_i k_i / n_i).
+    Each exponent is reduced in integers before it is evaluated.  For r = 2
+    the sum over k is written as e_1^T U e_2 with e_i[k_i] = exp(-2 pi i xi_i k_i / n_i):
+    O(N) per bin, no transform.
+    """
+    s = _shape(n)
+    N = int(np.prod(s))
+    U = np.asarray(u, dtype=np.complex128).reshape(s)
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.int64))
+    out = np.empty(xi.shape[0], dtype=np.complex128)
+    for t, row in enumerate(xi):
+        es = [np.exp(-2j * np.pi * ((int(row[i]) * np.arange(s[i], dtype=np.int64)) % s[i]) / s[i])
+              for i in range(len(s))]
+        acc = U
+        for e in reversed(es):
+            acc = acc @ e
+        out[t] = acc / N
+    return out
+
+
+def plane_wave_evolution(xi: np.ndarray, norms2: np.ndarray, c: np.ndarray, n, gamma: float,
+                         dt: float, nsteps: int, v_const: float, kappa: np.ndarray) -> np.ndarray:
+    """Exact state after nsteps Strang steps for u_0 = sum_j c_j exp(2 pi i h_j . x) and v = v_const.
+
+    A constant potential commutes with the Laplacian, so each Strang step is the
+    exact propagator (Sec. 2.4: the splitting error is a commutator): plane wave
+    h_j picks up exp(-i dt (v_const / gamma + gamma 2 pi^2 ||h_j||^2)) per step
+    (eq. Fourier-ODE for the kinetic part, eq. StrangTDSE for the potential).
+    This holds on the lattice when each h_j is the anti-aliasing representative
+    of its bin xi_j with norm norms2[j].  Returns u_N at the multi-indices
+    kappa (rows (k_1, ..., k_r)), with exp(2 pi i h . p_k) = exp(2 pi i sum_i xi_i k_i / n_i).
+    """
+    s = _shape(n)
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.int64))
+    kappa = np.atleast_2d(np.asarray(kappa, dtype=np.int64))
+    T = float(nsteps) * float(dt)
+    out = np.zeros(kappa.shape[0], dtype=np.complex128)
+    for j in range(xi.shape[0]):
+        ang = -T * (v_const / gamma + gamma * 2.0 * np.pi ** 2 * float(norms2[j]))
+        turns = np.zeros(kappa.shape[0], dtype=np.float64)
+        for i in range(len(s)):
+            turns += ((int(xi[j, i]) * kappa[:, i]) % s[i]) / s[i]
+        out += complex(c[j]) * np.exp(1j * ang) * np.exp(2j * np.pi * turns)
+    return out
+
+
+# --------------------------------------------------------------------------
 # Observables (Sec. 3.3)
 # --------------------------------------------------------------------------
 def norm2(u: np.ndarray) -> float:

@@ -19,7 +19,7 @@ LSP_OK = 0
 C64, C128 = 1, 2
 AA_MINL2, AA_EXPLICIT = 0, 1
 PHYSICAL, SPECTRAL = 0, 1
-PATH_MULTIPASS, PATH_SMALL = 0, 1
+PATH_MULTIPASS, PATH_SMALL, PATH_RANK2 = 0, 1, 2
 
 _lib = None
 _lock = threading.Lock()

@@ -144,16 +144,22 @@ static int minl2_dp(lsp_plan p, int32_t* out, int* box, int32_t* levels, int fix
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void build_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf, T* K,
-                             long long n, double turns_v, double turns_k, int multipass, int logN1, int logN2) {
+                             long long n, double turns_v, double turns_k, int order, int logN1, int logN2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double th = v[i] * turns_v;                       // -dt v / (4 pi gamma): half step, in turns
     T a, b, c;
     encode_phase(th, &a);
     encode_phase(2.0 * th, &b);
     long long bin = i;
-    if (multipass) {                                   // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
+    if (order == kPathMultipass) {                     // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
       long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
       bin = xi2 + (xi1 << logN2);
+    } else if (order == kPathRank2) {
+      // n1 = A B (A = 2^ceil(m1/2)): position (e + A g) n2 + xi2 <- bin (g + B e) n2 + xi2
+      const int la = (logN1 + 1) / 2, lb = logN1 - la;
+      long long xi2 = i & ((1ll << logN2) - 1), row = i >> logN2;
+      long long e = row & ((1ll << la) - 1), g = row >> la;
+      bin = ((g + (e << lb)) << logN2) + xi2;
     }
     encode_phase(turns_k * (double)norm2[bin], &c);
     Ph[i] = a;
@@ -189,14 +195,14 @@ static size_t csize(int prec) { return prec == LSP_C64 ? sizeof(float2) : sizeof
 int build_phase_tables(lsp_plan p, double dt, cudaStream_t s) {
   const double turns_v = -dt / (4.0 * M_PI * p->gamma);
   const double turns_k = -M_PI * p->gamma * dt;
-  const int mp = p->path == kPathMultipass;
+  const int order = p->path;
   if (p->prec == LSP_C64)
     build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
-                                                            (float2*)p->K, p->ntot, turns_v, turns_k, mp, p->logN1,
-                                                            p->logN2);
+                                                            (float2*)p->K, p->ntot, turns_v, turns_k, order,
+                                                            p->logN1, p->logN2);
   else
     build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
-                                                              (double2*)p->K, p->ntot, turns_v, turns_k, mp,
+                                                              (double2*)p->K, p->ntot, turns_v, turns_k, order,
                                                               p->logN1, p->logN2);
   return cuda_status(cudaGetLastError());
 }
@@ -355,6 +361,12 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
     p->path = kPathMultipass;
     p->logn = logn; p->logN1 = logN1; p->logN2 = logN2; p->N1 = 1 << logN1; p->N2 = 1 << logN2;
     p->logLmax = std::max(logN1, logN2);
+  } else if (r == 2 && !small_fits && ilog2exact(n[0]) > 0 && ilog2exact(n[1]) > 0 &&
+             r2_supports(prec, ilog2exact(n[0]), ilog2exact(n[1]))) {
+    // rank-2, both axes powers of two: row sweep along kappa_2, kappa_1 split in two column sweeps
+    p->path = kPathRank2;
+    p->logn = logn; p->logN1 = ilog2exact(n[0]); p->logN2 = ilog2exact(n[1]);
+    p->N1 = (int)n[1]; p->N2 = (int)n[0];
   } else if (small_fits) {
     p->path = kPathSmall;
     p->naxes = r;
@@ -404,6 +416,21 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
     if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN1); else fill_pass_twiddles<double2>(tw, p->logN1);
     p->twr_entries = (int)(tw.size() / sz);
     if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN2); else fill_pass_twiddles<double2>(tw, p->logN2);
+    if ((rc = dalloc(p, &p->tw_pass, std::max<size_t>(tw.size(), 16)))) return fail(rc);
+    if (cudaMemcpy(p->tw_pass, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
+  } else if (p->path == kPathRank2) {
+    if ((rc = dalloc(p, &p->work, ntot * sz))) return fail(rc);
+    if (prec == LSP_C64) fill_twiddles<float2>(tw, p->n[0], p->n[0]); else fill_twiddles<double2>(tw, p->n[0], p->n[0]);
+    if ((rc = dalloc(p, &p->tw_line, tw.size()))) return fail(rc);
+    if (cudaMemcpy(p->tw_line, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
+    tw.clear();
+    // line tables: rows (n2), then kappa_1 sub-lines of lengths A = 2^ceil(m1/2) and B = n1 / A
+    const int la = (p->logN1 + 1) / 2, lb = p->logN1 - la;
+    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN2); else fill_pass_twiddles<double2>(tw, p->logN2);
+    p->twr_entries = (int)(tw.size() / sz);
+    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, la); else fill_pass_twiddles<double2>(tw, la);
+    p->twa_entries = (int)(tw.size() / sz) - p->twr_entries;
+    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, lb); else fill_pass_twiddles<double2>(tw, lb);
     if ((rc = dalloc(p, &p->tw_pass, std::max<size_t>(tw.size(), 16)))) return fail(rc);
     if (cudaMemcpy(p->tw_pass, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
   } else {
@@ -461,7 +488,7 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
 
   // ---- kernel descriptors ----
   if (p->path == kPathMultipass) rc = multipass_upload_desc(p, 0);
-  else rc = small_upload_desc(p, 0);
+  else if (p->path == kPathSmall) rc = small_upload_desc(p, 0);
   if (rc) return fail(rc);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSP_ERR_CUDA);
   *out = p;
@@ -511,8 +538,9 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   int rc = build_phase_tables(p, dt, s);
   if (rc) return rc;
-  const int mp = p->path == kPathMultipass;
-  rc = mp ? multipass_steps(p, nsteps, s) : small_steps(p, nsteps, s);
+  rc = p->path == kPathMultipass ? multipass_steps(p, nsteps, s)
+       : p->path == kPathRank2   ? r2_steps_on(p, p->u, nsteps, s)
+                                 : small_steps(p, nsteps, s);
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return LSP_OK;
@@ -535,7 +563,9 @@ int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device,
   const void* src = p->u;
   int src_prec = p->prec;
   if (space == LSP_SPACE_SPECTRAL) {
-    int rc = p->path == kPathMultipass ? multipass_spectral(p, s) : small_spectral(p, s);
+    int rc = p->path == kPathMultipass ? multipass_spectral(p, s)
+             : p->path == kPathRank2   ? r2_spectral(p, s)
+                                       : small_spectral(p, s);
     if (rc) return rc;
     src = p->stage;
     src_prec = LSP_C128;
@@ -615,8 +645,8 @@ int lsp_index_table(lsp_plan p, int32_t* h) {
 int lsp_plan_info(lsp_plan p, int64_t* info) {
   if (!p || !info) return LSP_ERR_BAD_ARG;
   info[0] = p->ntot;
-  info[1] = p->path == kPathMultipass ? p->N1 : p->n[p->r - 1];
-  info[2] = p->path == kPathMultipass ? p->N2 : (p->r == 2 ? p->n[0] : 1);
+  info[1] = p->path != kPathSmall ? p->N1 : p->n[p->r - 1];
+  info[2] = p->path != kPathSmall ? p->N2 : (p->r == 2 ? p->n[0] : 1);
   info[3] = p->path;
   info[4] = p->prec;
   info[5] = (int64_t)p->bytes;

@@ -3,7 +3,9 @@
 //  * SMEM-resident instances: one launch, one CTA per instance, all steps;
 //  * multipass instances: one group per lattice size 2^m (kernels are
 //    specialised per size); each group is a head sweep, one persistent
-//    cooperative launch over the tiles of all its instances, and a tail sweep.
+//    cooperative launch over the tiles of all its instances, and a tail sweep;
+//  * rank-2 multipass instances (2^26 points and the like, each enough to
+//    fill the GPU): stepped one after another.
 // Each instance's phase tables are built with its own dt on every call.
 #include <string.h>
 
@@ -63,6 +65,7 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   std::map<int, std::vector<int>> by_m;
   for (int i = 0; i < count; ++i) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
+    else if (plans[i]->path == kPathRank2) b->rank2_ids.push_back(i);
     else b->small_ids.push_back(i);
   }
   // SMEM-resident group
@@ -126,6 +129,10 @@ int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream)
   }
   if (!b->small_ids.empty()) {
     int rc = small_batch_launch(b->prec, b->small_desc, (int)b->small_ids.size(), b->small_max_n, nsteps, s);
+    if (rc) return rc;
+  }
+  for (int i : b->rank2_ids) {   // each fills the GPU by itself
+    int rc = r2_steps_on(b->plans[i], b->plans[i]->u, nsteps, s);
     if (rc) return rc;
   }
   for (auto& c : b->classes) {

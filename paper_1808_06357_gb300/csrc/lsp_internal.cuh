@@ -30,7 +30,7 @@ constexpr int kSmallThreads = 512;
 // Bounded device-side waits (grid barrier): spins of ~100 ns each.
 constexpr long long kSpinLimit = 1ll << 25;
 
-enum PathKind { kPathMultipass = 0, kPathSmall = 1 };
+enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2 };
 
 // --------------------------------------------------------------------------
 // Plan
@@ -56,7 +56,8 @@ struct lsp_plan_s {
   int aa_mode = LSP_AA_MINL2;
   int path = lsp::kPathSmall;
 
-  // multipass geometry (rank-1, n = N1 * N2, row length N1 contiguous)
+  // multipass geometry (rank-1, n = N1 * N2, row length N1 contiguous;
+  // rank-2 multipass: logN1 = log2 n_1, logN2 = log2 n_2)
   int logn = 0, N1 = 1, N2 = 1, logN1 = 0, logN2 = 0, logLmax = 0;
 
   // SMEM-resident geometry
@@ -71,10 +72,11 @@ struct lsp_plan_s {
   void* Ph = nullptr;         // exp(-i dt v / (2 gamma)), kappa order, encoded
   void* Pf = nullptr;         // exp(-i dt v / gamma), kappa order, encoded
   void* K = nullptr;          // exp(-i gamma 2 pi^2 |h|^2 dt) in the kernel's bin order
-  void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (multipass)
+  void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (multipass); W_n1^k, k < n1 (rank-2 multipass)
   void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (multipass)
   void* tw_pass = nullptr;    // per-pass line twiddles: row lines, then column lines
   int twr_entries = 0;        // entries of the row-line part of tw_pass
+  int twa_entries = 0;        // rank-2: entries of the second part (the third follows)
   void* tw_small = nullptr;   // per-axis W_len^k tables (SMEM-resident path)
   void* stage = nullptr;      // n complex128 staging buffer (conversions, spectral output)
   void* work = nullptr;       // n complex (plan precision): scratch copy for spectral output
@@ -93,6 +95,7 @@ struct lsp_plan_s {
 struct lsp_batch_s {
   std::vector<lsp_plan> plans;   // borrowed
   int prec = LSP_C64;
+  std::vector<int> rank2_ids;    // rank-2 multipass instances, stepped one after another
   int device = 0;
   // SMEM-resident instances: one CTA each, one launch for all of them
   std::vector<int> small_ids;
@@ -211,6 +214,11 @@ int multipass_desc_size(int prec);
 void multipass_fill_desc(lsp_plan p, void* host_out, int* ncol, int* nrow);
 int multipass_batch_steps(int prec, int m, const void* ddesc, const int2* colmap, const int2* rowmap, int ninst,
                           int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s);
+
+// rank-2 multipass (n_1 = 2^m1, n_2 = 2^m2)
+bool r2_supports(int prec, int m1, int m2);
+int r2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
+int r2_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; }
 

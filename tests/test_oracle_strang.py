@@ -245,3 +245,54 @@ def test_adjoint_checkpoint_stride_invariance():
     a = S.strang_adjoint(u0, v, dp, n, 0.1, 0.01, 10, phi, ckpt=1)
     b = S.strang_adjoint(u0, v, dp, n, 0.1, 0.01, 10, phi, ckpt=7)
     assert np.allclose(a[1], b[1], atol=1e-14) and np.allclose(a[2], b[2], atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Spot-check helpers (coeff_at, plane_wave_evolution)
+# --------------------------------------------------------------------------
+RANK2_SMALL = [(w.c5(10, 8, 16, 6).Z, (1024, 256))]
+
+
+@pytest.mark.parametrize("Z,n", CASES + RANK2_SMALL)
+def test_coeff_at_equals_direct_lattice_rule(Z, n):
+    """coeff_at (multi-index form, integer-reduced exponents) equals eq. approx_uhat summed
+    over the lattice points with the vectors h themselves."""
+    P = L.lattice_points(Z, n)
+    rng = np.random.default_rng(5)
+    u = _rand_c(rng, P.shape[0])
+    d = P.shape[1]
+    H = rng.integers(-3, 4, size=(6, d))
+    xi = L.residues(H, Z, n)
+    got = S.coeff_at(u, n, xi)
+    assert np.allclose(got, S.lattice_rule_coeffs(u, P, H), rtol=0, atol=1e-12 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("Z,n", CASES + RANK2_SMALL)
+def test_plane_wave_evolution_equals_strang_run(Z, n):
+    """Closed-form constant-potential evolution of a few plane waves equals the FFT Strang loop."""
+    norms, _ = L.minl2_norms_dp(Z, n)
+    rng = np.random.default_rng(6)
+    N = int(np.prod(n))
+    bins = rng.choice(N, size=5, replace=False)
+    xi = np.stack(np.unravel_index(bins, n), axis=1)
+    c = _rand_c(rng, 5)
+    u0 = w.plane_waves(xi, c, n)
+    gamma, dt, nsteps, vc = 0.1, 2e-3, 40, 0.7
+    ref = S.strang(u0, np.full(N, vc), norms, n, gamma, dt, nsteps)
+    kappa = np.stack(np.unravel_index(np.arange(N), n), axis=1)
+    got = S.plane_wave_evolution(xi, norms[bins], c, n, gamma, dt, nsteps, vc, kappa)
+    assert np.allclose(got, ref, rtol=0, atol=1e-11)
+
+
+def test_c5_small_norm_vectors_are_their_bins_representatives():
+    """For the C5 lattice (HC bound 16, d = 16) every h with ||h||^2 <= 4 lies in the hyperbolic
+    cross, on which h -> xi is injective, so h is the unique minimal-norm vector of its bin:
+    the min-l2 norm of its bin is ||h||^2.  Checked here on the full-size generating vectors."""
+    inst = w.c5()
+    B = L.ball_points(16, 2.0)
+    HC = w.hyperbolic_cross(16, 16)
+    hc = {tuple(r) for r in HC.tolist()}
+    assert all(tuple(r) in hc for r in B.tolist())
+    xi = L.residues(HC, inst.Z, inst.n)
+    keys = xi[:, 0] * inst.n[1] + xi[:, 1]
+    assert np.unique(keys).size == HC.shape[0]

@@ -1,0 +1,48 @@
+"""Input generators: lattices in canonical form, fast field evaluation (no GPU)."""
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+import workloads as w
+
+
+@pytest.mark.parametrize("shape,bound", [((10, 8), 6), ((11, 9), 8), ((8, 6), 4)])
+def test_rank2_generator_gives_canonical_injective_lattices(shape, bound):
+    inst = w.c5(*shape, 16, bound)
+    assert L.is_canonical(inst.Z, inst.n)
+    assert L.is_anti_aliasing(w.hyperbolic_cross(16, bound), inst.Z, inst.n)
+
+
+def test_units_in_every_component_merge_points_for_even_moduli():
+    """Def. 1 asks each component of z_i to be prime to n_i; with n_1, n_2 even and every
+    component odd the image of h -> (h.z_1, h.z_2) mod 2 is the diagonal, so the points
+    k and k + (n_1/2, n_2/2) coincide and the lattice has fewer than n_1 n_2 points."""
+    Z = np.array([[1, 3], [5, 7], [9, 1]])
+    n = (16, 8)
+    assert not L.is_canonical(Z, n)
+    q = L.lattice_numerators(Z, n)
+    k = np.array([8, 4])
+    assert np.array_equal(q[k[0] * n[1] + k[1]], q[0])
+
+
+def test_c5_fields_equal_direct_evaluation():
+    inst = w.c5(10, 8, 16, 6)
+    P = L.lattice_points(inst.Z, inst.n)
+    v, u = w.c5_fields(inst, rows_per_chunk=100)
+    assert np.allclose(v, inst.v(P), rtol=0, atol=1e-12)
+    assert np.allclose(u, inst.u0(P), rtol=1e-12, atol=0)
+
+
+def test_plane_waves_equal_exponentials_at_points():
+    inst = w.c5(8, 6, 16, 4)
+    P = L.lattice_points(inst.Z, inst.n)
+    H = np.zeros((3, 16), dtype=np.int64)
+    H[0, 0] = 1
+    H[1, 3], H[1, 7] = 1, -1
+    H[2, 12] = 2
+    c = np.array([1.0, 0.5j, -0.25 + 0.1j])
+    xi = L.residues(H, inst.Z, inst.n)
+    got = w.plane_waves(xi, c, inst.n)
+    ref = np.exp(2j * np.pi * (P @ H.T.astype(np.float64))) @ c
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)

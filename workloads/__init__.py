@@ -228,7 +228,15 @@ def reconstructing_rank1(index_set: np.ndarray, n: int, rng: Rng,
 
 def reconstructing_rank2(index_set: np.ndarray, n1: int, n2: int, rng: Rng,
                          tries: int = 4000) -> np.ndarray:
-    """Seeded search for Z = (z_1, z_2) with h -> (h.z_1 mod n1, h.z_2 mod n2) injective on I."""
+    """Seeded search for Z = (z_1, z_2) with h -> (h.z_1 mod n1, h.z_2 mod n2) injective on I.
+
+    Component 0 is fixed to (1, 0) and every later component is (a, b) with a a
+    unit mod n1 and b a unit mod n2, so (1, 0) and (0, 1) lie in the image of
+    h -> (h.z_1, h.z_2): the map onto Z_n1 x Z_n2 is surjective and the n1 n2
+    lattice points are distinct.  (With n1, n2 both even, making every
+    component of z_2 a unit as well would confine the image mod 2 to the
+    diagonal and merge the points k and k + (n1/2, n2/2).)
+    """
     I = np.asarray(index_set, dtype=np.int64)
     d = I.shape[1]
     z1, z2 = [1], [0]
@@ -247,21 +255,6 @@ def reconstructing_rank2(index_set: np.ndarray, n1: int, n2: int, rng: Rng,
                 break
         else:
             raise RuntimeError(f"no injective component {j} found")
-    # z_2 starts with 0 in the first coordinate: replace by a unit so every
-    # component of z_2 is prime to n2 (canonical form, Def. 1) while keeping
-    # injectivity on I.
-    for _ in range(tries):
-        b = int(rng.integers(1, 1, n2)[0])
-        if math.gcd(b, n2) != 1:
-            continue
-        zz2 = [b] + z2[1:]
-        k1 = (I @ np.array(z1, dtype=np.int64)) % n1
-        k2 = (I @ np.array(zz2, dtype=np.int64)) % n2
-        if _distinct(k1 * n2 + k2):
-            z2 = zz2
-            break
-    else:
-        raise RuntimeError("no canonical z_2 found")
     return np.stack([np.array(z1, dtype=np.int64), np.array(z2, dtype=np.int64)], axis=1)
 
 
@@ -278,6 +271,62 @@ def random_rank1(d: int, n: int, rng: Rng) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Workload descriptions
 # --------------------------------------------------------------------------
+def plane_waves(xi: np.ndarray, c: Sequence[complex], n) -> np.ndarray:
+    """u_k = sum_j c_j exp(2 pi i sum_i xi_ji k_i / n_i) for every multi-index k (lexicographic).
+
+    This is the sum of the plane waves exp(2 pi i h_j . x) sampled at the
+    lattice points, h_j . z_i = xi_ji mod n_i.  Exponents are reduced in
+    integers; each term is an outer product of one-dimensional factors.
+    """
+    s = tuple(int(x) for x in np.atleast_1d(n))
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.int64))
+    out = np.zeros(s, dtype=np.complex128)
+    for j in range(xi.shape[0]):
+        term = np.array(complex(c[j]), dtype=np.complex128)
+        for i in range(len(s)):
+            e = np.exp(2j * np.pi * ((int(xi[j, i]) * np.arange(s[i], dtype=np.int64)) % s[i]) / s[i])
+            term = np.multiply.outer(term, e)
+        out += term
+    return out.reshape(-1)
+
+
+def c5_fields(inst: "Instance", rows_per_chunk: int = 256):
+    """C5's v (v_pair_cos) and u0 (product Gaussian, sigma 0.1 at 0.5) on a rank-2 lattice.
+
+    Evaluated without materialising the (N, d) point array: coordinate j of
+    point (k1, k2) is t_j / n1 with t_j = (z1_j k1 + z2_j k2 n1 / n2) mod n1,
+    so every one-dimensional factor is a lookup in a table of n1 values, and
+    sum_{j<k} cos 2 pi (x_j - x_k) = (|sum_j exp(2 pi i x_j)|^2 - d) / 2.
+    Same values as v_pair_cos and gaussian_packet on lattice_points up to
+    rounding; the discrete normalisation is the same.
+    """
+    n1, n2 = int(inst.n[0]), int(inst.n[1])
+    Zm = inst.Zmat.astype(np.int64) % np.array([n1, n2], dtype=np.int64)
+    d = Zm.shape[0]
+    t = np.arange(n1, dtype=np.int64)
+    etab = np.exp(2j * np.pi * t / n1)
+    gtab = periodized_gaussian(t / n1, 0.5, 0.1)
+    step2 = n1 // n2
+    k2 = np.arange(n2, dtype=np.int64)
+    col = [(Zm[j, 1] * step2 * k2) % n1 for j in range(d)]
+    v = np.empty(n1 * n2, dtype=np.float64)
+    u = np.empty(n1 * n2, dtype=np.complex128)
+    for r0 in range(0, n1, rows_per_chunk):
+        k1 = np.arange(r0, min(n1, r0 + rows_per_chunk), dtype=np.int64)
+        acc = np.zeros((k1.size, n2), dtype=np.complex128)
+        amp = np.ones((k1.size, n2), dtype=np.float64)
+        for j in range(d):
+            tj = ((Zm[j, 0] * k1) % n1)[:, None] + col[j][None, :]
+            tj %= n1
+            acc += etab[tj]
+            amp *= gtab[tj]
+        sl = slice(r0 * n2, (r0 + k1.size) * n2)
+        v[sl] = (0.05 * (np.abs(acc) ** 2 - d)).reshape(-1)
+        u[sl] = amp.reshape(-1)
+    u /= math.sqrt(float(np.mean(np.abs(u) ** 2)))
+    return v, u
+
+
 @dataclass
 class Instance:
     """One TDSE problem: lattice, physics parameters and input functions."""
