@@ -41,20 +41,43 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched measurement")
+    ap.add_argument("--no-rank2", action="store_true", help="skip the rank-2 2^14 x 2^12 batch measurement")
     ap.add_argument("--log2n", type=int, default=22, help="lattice size 2^m of the d=6 workload (profiling)")
     ap.add_argument("--inner", type=int, default=STEPS_PER_CALL, help="Strang steps per bench step")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
+                    help="c2: the headline run (with its side measurements); c5: only the rank-2 "
+                         "2^14 x 2^12 batch (profiling; --inner steps per call, --batch instances)")
+    ap.add_argument("--batch", type=int, default=4, help="instances of the c5 workload")
     return ap.parse_args()
 
 
-def csrc_digest() -> str:
-    """Checksum of the CUDA sources (identifies the kernels an ncu record belongs to)."""
-    import glob
+# CUDA sources each profiled kernel family is built from
+KERNEL_SOURCES = {
+    "mp_persistent": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_mp.cuh", "lsp_mp_c64_hi.cu"],
+    "r2_sweep": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_mp.cuh", "lsp_r2.cu"],
+}
+
+
+def csrc_digest(family: str) -> str:
+    """Checksum of the sources of one kernel family (identifies the kernels an ncu record belongs to)."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1808_06357_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES[family]:
+        with open(os.path.join(ROOT, "paper_1808_06357_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def traffic_record(name: str, family: str):
+    """DRAM bytes per launch from a committed ncu record, if it was taken on the current sources."""
+    prof = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
+    try:
+        rec = json.load(open(prof))
+        if rec.get("csrc_sha256_16") == csrc_digest(family):
+            return rec
+    except Exception:
+        pass
+    return None
 
 
 def peaks():
@@ -203,6 +226,30 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_c5(args):
+    """Only the rank-2 batch (complex64): a profiling entry with a short, configurable run."""
+    import torch
+
+    import paper_1808_06357_gb300 as lsp
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clk = Clocks(local)
+    clk.start()
+    r = measure_rank2(args, lsp, torch, dev, local, flush, stream, world, precs=("c64",), nsteps=args.inner,
+                      count=args.batch, calls64=args.steps)
+    clocks = clk.stop()
+    if rank == 0:
+        c = r["c64"]
+        print(json.dumps({"metric": METRIC, "value": c["value"], "unit": c["unit"], "n_gpus": world,
+                          "steps": args.steps, "warmup": 1, "ms_per_step": c["ms_per_call"],
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": r["workload"]}, "roofline": c["roofline"],
+                          "clocks": clocks}))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -269,15 +316,9 @@ def run_ours(args):
     kern_s = statistics.mean(ms) / 1e3
     achieved = alg_bytes / kern_s / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic_c64_n2p22.json")
-    if os.path.exists(prof) and args.log2n == 22 and STEPS_PER_CALL == 1000:
-        try:
-            rec = json.load(open(prof))
-            # counters are valid only for the kernel sources they were taken on
-            if rec.get("csrc_sha256_16") == csrc_digest():
-                traffic = rec.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    if args.log2n == 22 and STEPS_PER_CALL == 1000:
+        rec = traffic_record("c64_n2p22", "mp_persistent")   # None once the kernel sources changed
+        traffic = rec.get("bytes_per_launch") if rec else None
 
     # complex128 side measurement on the same workload
     c128 = None
@@ -325,6 +366,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched and args.log2n == 22:
         batched = measure_batched(args, lsp, torch, dev, local, flush, stream, world)
+    rank2 = None
+    if not args.no_rank2:
+        rank2 = measure_rank2(args, lsp, torch, dev, local, flush, stream, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -347,6 +391,7 @@ def run_ours(args):
                          "alg_bytes_per_point_step": 48},
             "complex128": c128,
             "batched": batched,
+            "rank2": rank2,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
@@ -408,10 +453,68 @@ def measure_batched(args, lsp, torch, dev, local, flush, stream, world):
     return out
 
 
+def measure_rank2(args, lsp, torch, dev, local, flush, stream, world, precs=("c64", "c128"), nsteps=None,
+                  count=None, calls64=2):
+    """Rank-2 lattice 2^14 x 2^12 (2^26 points), d = 16, batch of 4 instances advanced
+    200 steps per call through lsp_batch_steps, complex64 and complex128.  Each
+    instance's state (0.5 / 1 GiB) exceeds L2."""
+    import workloads as w
+    inst = w.c5()
+    v_h, u_h = w.c5_fields(inst)
+    v_d = torch.from_numpy(v_h).to(dev)
+    n = inst.npoints
+    nsteps = inst.nsteps if nsteps is None else nsteps
+    count = inst.extra["batch"] if count is None else count
+    hbm, _ = peaks()
+    out = {"workload": "rank-2 lattice d=16, n1 x n2 = 2^14 x 2^12 (2^26 points), HC(16) reconstructing Z, "
+                       "MINL2 set, v = sum_{j<k} 0.1 cos 2 pi (x_j - x_k), product Gaussian, gamma=0.1, "
+                       f"dt=1e-3, batch of {count}, {nsteps} steps per call"}
+    for prec, cb, calls in (("c64", 8, calls64), ("c128", 16, 1)):
+        if prec not in precs:
+            continue
+        cdt = torch.complex64 if prec == "c64" else torch.complex128
+        u_d = torch.from_numpy(u_h).to(dev).to(cdt)
+        plans = [lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec, device=local) for _ in range(count)]
+        for p in plans:
+            p.set_potential(v_d)
+            p.set_state(u_d)
+        batch = lsp.Batch(plans)
+        dts = [inst.dt] * count
+        batch.steps(dts, 5)                                 # warm-up
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(calls):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.steps(dts, nsteps)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        if batch.status() != 0:
+            raise RuntimeError("rank-2 batch status " + lsp.strerror(batch.status()))
+        t = max_over_ranks(sum(ms), world) / 1e3
+        mean_s = statistics.mean(ms) / 1e3
+        achieved = 6 * cb * n * count * nsteps / mean_s / 1e9
+        out[prec] = {"value": world * n * count * nsteps * calls / t, "unit": "lattice-point steps/s",
+                     "timed_calls": calls, "ms_per_call": 1e3 * t / calls,
+                     "roofline": {"bound": "hbm" if prec == "c64" else "alu", "achieved": achieved, "peak": hbm,
+                                  "unit": "GB/s", "frac": achieved / hbm,
+                                  "alg_bytes_per_point_step": 6 * cb, "sweep_bytes_per_point_step": 10 * cb}}
+        batch.destroy()
+        for p in plans:
+            p.destroy()
+        del u_d
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c5":
+        run_c5(args)
     else:
         run_ours(args)
 

@@ -142,14 +142,21 @@ static int minl2_dp(lsp_plan p, int32_t* out, int* box, int32_t* levels, int fix
 // Phase tables (Algorithm 1: diagonals of exp(-i dt V/(2 gamma)), exp(-i gamma D dt / 2)),
 // arguments reduced mod 2 pi in FP64.
 // ---------------------------------------------------------------------------
+// K depends on the bin only through the integer ||h_chi||^2: one value per norm.
+template <typename T>
+__global__ void build_klut(T* lut, int count, double turns_k) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < count; m += gridDim.x * blockDim.x)
+    encode_phase(turns_k * (double)m, &lut[m]);
+}
+
 template <typename T>
 __global__ void build_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf, T* K,
-                             long long n, double turns_v, double turns_k, int order, int logN1, int logN2) {
+                             const T* __restrict__ klut, long long n, double turns_v, double turns_k, int order,
+                             int logN1, int logN2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double th = v[i] * turns_v;                       // -dt v / (4 pi gamma): half step, in turns
     T a, b, c;
-    encode_phase(th, &a);
-    encode_phase(2.0 * th, &b);
+    encode_phase_pair(th, &a, &b);
     long long bin = i;
     if (order == kPathMultipass) {                     // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
       long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
@@ -161,7 +168,8 @@ __global__ void build_tables(const double* __restrict__ v, const int32_t* __rest
       long long e = row & ((1ll << la) - 1), g = row >> la;
       bin = ((g + (e << lb)) << logN2) + xi2;
     }
-    encode_phase(turns_k * (double)norm2[bin], &c);
+    if (klut) c = klut[norm2[bin]];
+    else encode_phase(turns_k * (double)norm2[bin], &c);
     Ph[i] = a;
     Pf[i] = b;
     K[i] = c;
@@ -196,14 +204,18 @@ int build_phase_tables(lsp_plan p, double dt, cudaStream_t s) {
   const double turns_v = -dt / (4.0 * M_PI * p->gamma);
   const double turns_k = -M_PI * p->gamma * dt;
   const int order = p->path;
-  if (p->prec == LSP_C64)
+  const int nlut = p->klut ? (int)p->max_norm2 + 1 : 0;
+  if (p->prec == LSP_C64) {
+    if (nlut) build_klut<float2><<<(nlut + 255) / 256, 256, 0, s>>>((float2*)p->klut, nlut, turns_k);
     build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
-                                                            (float2*)p->K, p->ntot, turns_v, turns_k, order,
-                                                            p->logN1, p->logN2);
-  else
+                                                            (float2*)p->K, (const float2*)p->klut, p->ntot, turns_v,
+                                                            turns_k, order, p->logN1, p->logN2);
+  } else {
+    if (nlut) build_klut<double2><<<(nlut + 255) / 256, 256, 0, s>>>((double2*)p->klut, nlut, turns_k);
     build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
-                                                              (double2*)p->K, p->ntot, turns_v, turns_k, order,
-                                                              p->logN1, p->logN2);
+                                                              (double2*)p->K, (const double2*)p->klut, p->ntot,
+                                                              turns_v, turns_k, order, p->logN1, p->logN2);
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -280,8 +292,8 @@ static void free_plan(lsp_plan p) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
-  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->tw_line, p->tw_fine, p->tw_pass, p->tw_small,
-                  p->stage, p->work, p->desc, p->bar, p->err};
+  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->klut, p->tw_line, p->tw_fine, p->tw_pass,
+                  p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
   for (void* b : bufs) if (b) cudaFree(b);
   if (p->err_host) cudaFreeHost(p->err_host);
   cudaSetDevice(prev);
@@ -485,6 +497,7 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
     cudaFree(dmax);
     p->max_norm2 = mx;
   }
+  if (p->max_norm2 < kKLutMax && (rc = dalloc(p, &p->klut, (p->max_norm2 + 1) * sz))) return fail(rc);
 
   // ---- kernel descriptors ----
   if (p->path == kPathMultipass) rc = multipass_upload_desc(p, 0);

@@ -27,6 +27,8 @@ constexpr int kMinColsC128 = 4;
 // SMEM-resident path: two state copies must fit in shared memory.
 constexpr int kSmallSmemBytes = 200 * 1024;
 constexpr int kSmallThreads = 512;
+// Largest ||h||^2 for which K is tabulated per norm value.
+constexpr long long kKLutMax = 1ll << 20;
 // Bounded device-side waits (grid barrier): spins of ~100 ns each.
 constexpr long long kSpinLimit = 1ll << 25;
 
@@ -72,6 +74,7 @@ struct lsp_plan_s {
   void* Ph = nullptr;         // exp(-i dt v / (2 gamma)), kappa order, encoded
   void* Pf = nullptr;         // exp(-i dt v / gamma), kappa order, encoded
   void* K = nullptr;          // exp(-i gamma 2 pi^2 |h|^2 dt) in the kernel's bin order
+  void* klut = nullptr;       // K per value of ||h||^2 = 0..max_norm2 (when max_norm2 < kKLutMax)
   void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (multipass); W_n1^k, k < n1 (rank-2 multipass)
   void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (multipass)
   void* tw_pass = nullptr;    // per-pass line twiddles: row lines, then column lines
@@ -163,22 +166,62 @@ __host__ __device__ inline void encode_phase(double turns, double2* out) {
   *out = double2{c, s};
 }
 
+__host__ __device__ inline float2 encode_half_angle(double r, double sh, double ch);
+
 __host__ __device__ inline void encode_phase(double turns, float2* out) {
-  double r = turns - rint(turns);            // [-1/2, 1/2]
-  int h = 0;
-  if (r > 0.25) { r -= 0.5; h = 1; }
-  else if (r < -0.25) { r += 0.5; h = 1; }
+  const double r = turns - rint(turns);      // [-1/2, 1/2]
+  // one FP64 sine/cosine pair of the half angle: sin(phi) = 2 sin(phi/2) cos(phi/2)
 #ifdef __CUDA_ARCH__
-  double sh = sinpi(r);                      // sin(phi/2), phi = 2 pi r
-  double s = sinpi(2.0 * r);
+  double sh, ch;
+  sincospi(r, &sh, &ch);                     // phi = 2 pi r
 #else
-  double sh = sin(3.14159265358979323846 * r);
-  double s = sin(2.0 * 3.14159265358979323846 * r);
+  double sh = sin(3.14159265358979323846 * r), ch = cos(3.14159265358979323846 * r);
 #endif
-  double c = -2.0 * sh * sh;                 // cos(phi) - 1
-  float af = fabsf((float)c);                // |c|, +0.0 when c is -0.0
-  float stored = h ? af : -af;               // sign bit set <=> h = 0 (also -0.0)
-  *out = float2{stored, (float)s};
+  *out = encode_half_angle(r, sh, ch);
+}
+
+// The pair (phi, 2 phi) from one FP64 sine/cosine evaluation, as encode_phase
+// of turns and of 2 turns (the half and full potential steps).
+//   complex128: (cos 2 phi, sin 2 phi) from (cos phi, sin phi) by the double-angle formulas.
+//   complex64 : from sin(pi r), cos(pi r), r = turns reduced to [-1/2, 1/2]:
+//     sin(2 pi r) and cos(2 pi r) are the half-angle pair of 2 r, shifted by
+//     rint(2 r) half turns; the half-turn fold of encode_phase is applied to each.
+__host__ __device__ inline void encode_phase_pair(double turns, double2* half, double2* full) {
+  double r = turns - rint(turns);
+#ifdef __CUDA_ARCH__
+  double s, c;
+  sincospi(2.0 * r, &s, &c);
+#else
+  double s = sin(2.0 * 3.14159265358979323846 * r), c = cos(2.0 * 3.14159265358979323846 * r);
+#endif
+  *half = double2{c, s};
+  *full = double2{1.0 - 2.0 * s * s, 2.0 * s * c};
+}
+
+__host__ __device__ inline float2 encode_half_angle(double r, double sh, double ch) {
+  // r in [-1/2, 1/2], sh = sin(pi r), ch = cos(pi r)
+  int h = 0;
+  if (r > 0.25) { const double t = sh; sh = -ch; ch = t; h = 1; }        // r - 1/2
+  else if (r < -0.25) { const double t = sh; sh = ch; ch = -t; h = 1; }  // r + 1/2
+  const double s = 2.0 * sh * ch;
+  const double c = -2.0 * sh * sh;
+  const float af = fabsf((float)c);
+  return float2{h ? af : -af, (float)s};
+}
+
+__host__ __device__ inline void encode_phase_pair(double turns, float2* half, float2* full) {
+  const double r = turns - rint(turns);
+#ifdef __CUDA_ARCH__
+  double sh, ch;
+  sincospi(r, &sh, &ch);
+#else
+  double sh = sin(3.14159265358979323846 * r), ch = cos(3.14159265358979323846 * r);
+#endif
+  *half = encode_half_angle(r, sh, ch);
+  const double k = rint(2.0 * r);                  // -1, 0 or 1
+  const double r2 = 2.0 * r - k;                   // 2 turns reduced, exactly
+  const double sg = k == 0.0 ? 1.0 : -1.0;
+  *full = encode_half_angle(r2, sg * 2.0 * sh * ch, sg * (1.0 - 2.0 * sh * sh));
 }
 
 __device__ __forceinline__ float2 apply_phase(float2 x, float2 e) {

@@ -64,8 +64,17 @@ template <typename T> struct MPParams {
 // NT threads per worker, NW workers per CTA, TILE elements per worker tile
 // (16 per thread), minimum resident CTAs per SM (register budget).
 template <typename T> struct Cfg;
+#ifndef LSP_MP_NT_C64
+#define LSP_MP_NT_C64 512
+#endif
+#ifndef LSP_MP_TW_SMEM
+#define LSP_MP_TW_SMEM 1
+#endif
+#ifndef LSP_MP_SWEEPS
+#define LSP_MP_SWEEPS 0
+#endif
 template <> struct Cfg<float2> {
-  static constexpr int NT = 512, NW = 1, TILE = 8192, MINB = LSP_MINB_C64;
+  static constexpr int NT = LSP_MP_NT_C64, NW = 1, TILE = 16 * NT, MINB = LSP_MINB_C64;
 };
 template <> struct Cfg<double2> {
   static constexpr int NT = 256, NW = 1, TILE = 4096, MINB = LSP_MINB_C128;
@@ -91,7 +100,7 @@ template <typename T, int M> struct SmemLayout {
   static constexpr int twl = twc + ColLine<T, M>::TW_ENTRIES;
   static constexpr int twf = twl + (1 << Split<M>::LN1);
   static constexpr int elems_all = twf + (1 << Split<M>::LN2);
-  static constexpr bool tw_in_smem = (size_t)elems_all * sizeof(T) <= 227u * 1024u - 256u;
+  static constexpr bool tw_in_smem = LSP_MP_TW_SMEM && (size_t)elems_all * sizeof(T) <= 227u * 1024u - 256u;
   static constexpr size_t bytes = (size_t)(tw_in_smem ? elems_all : twr) * sizeof(T);
 };
 
@@ -470,6 +479,10 @@ template <typename T, int M> MPKernels mp_kernels_for() {
   MPKernels k;
   k.persistent = (const void*)mp_persistent<T, NT, M>;
   k.persistent_smem = SmemLayout<T, M>::bytes;
+#if LSP_MP_SWEEPS
+  k.sweep[kMid] = (const void*)mp_sweep<T, NT, M, kMid>;
+  k.sweep[kRow] = (const void*)mp_sweep<T, NT, M, kRow>;
+#endif
   k.sweep[kHead] = (const void*)mp_sweep<T, NT, M, kHead>;
   k.sweep[kTail] = (const void*)mp_sweep<T, NT, M, kTail>;
   k.sweep[kColFwd] = (const void*)mp_sweep<T, NT, M, kColFwd>;

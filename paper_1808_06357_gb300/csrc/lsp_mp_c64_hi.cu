@@ -11,7 +11,9 @@ bool mp_kernels_c64_hi(int m, MPKernels* k) {
     case 20: *k = mp_kernels_for<float2, 20>(); return true;
     case 21: *k = mp_kernels_for<float2, 21>(); return true;
     case 22: *k = mp_kernels_for<float2, 22>(); return true;
+#if LSP_MP_NT_C64 >= 512   // rows of 2^13 points need 8192-point tiles
     case 23: *k = mp_kernels_for<float2, 23>(); return true;
+#endif
     default: return false;
   }
 }

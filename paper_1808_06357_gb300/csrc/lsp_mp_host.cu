@@ -119,13 +119,30 @@ int multipass_upload_desc(lsp_plan p, cudaStream_t s) {
   return p->prec == LSP_C64 ? upload_desc_impl<float2>(p, s) : upload_desc_impl<double2>(p, s);
 }
 
-// head sweep, persistent kernel for sweeps 1..2N-1, tail sweep
+// Sweeps 1..2N-1 of N steps (row, mid, ..., row): one persistent cooperative
+// launch, or (LSP_MP_SWEEPS) one launch per sweep.
+template <typename T>
+static int middle_sweeps(int m, const MPInst<T>* d, const int2* colmap, const int2* rowmap, int ninst, int total_col,
+                         int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
+#if LSP_MP_SWEEPS
+  int rc = LSP_OK;
+  for (int64_t k = 0; k < nsteps && !rc; ++k) {
+    rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kRow, s);
+    if (!rc && k + 1 < nsteps) rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kMid, s);
+  }
+  return rc;
+#else
+  return launch_persistent<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
+#endif
+}
+
+// head sweep, sweeps 1..2N-1, tail sweep
 template <typename T>
 static int steps_impl(lsp_plan p, int64_t nsteps, cudaStream_t s) {
   MPInst<T> I = make_inst<T>(p, nullptr);
   const MPInst<T>* d = (const MPInst<T>*)p->desc;
   int rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kHead, s);
-  if (!rc) rc = launch_persistent<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
+  if (!rc) rc = middle_sweeps<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
   if (!rc) rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kTail, s);
   return rc;
 }
@@ -139,7 +156,7 @@ static int steps_on_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s
   MPInst<T>* d = (MPInst<T>*)p->desc + 2;
   LSP_CUDA_TRY(cudaMemcpyAsync(d, &I, sizeof(I), cudaMemcpyHostToDevice, s));
   int rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kHead, s);
-  if (!rc) rc = launch_persistent<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
+  if (!rc) rc = middle_sweeps<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
   if (!rc) rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kTail, s);
   return rc;
 }
@@ -192,7 +209,7 @@ static int batch_impl(int m, const void* ddesc, const int2* colmap, const int2* 
                       int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
   const MPInst<T>* d = (const MPInst<T>*)ddesc;
   int rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kHead, s);
-  if (!rc) rc = launch_persistent<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
+  if (!rc) rc = middle_sweeps<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
   if (!rc) rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kTail, s);
   return rc;
 }

@@ -20,7 +20,7 @@
 #include <mutex>
 #include <utility>
 
-#include "lsp_tile.cuh"
+#include "lsp_mp.cuh"
 
 namespace lsp {
 
@@ -31,188 +31,238 @@ template <typename T> struct R2Inst {
   const T* Pf;
   const T* K;
   const T* tw_rows;   // per-pass twiddles, lines of length n2
-  const T* tw_a;      // ... of length LA
-  const T* tw_b;      // ... of length LB
+  const T* tw_a;      // ... of length A
+  const T* tw_b;      // ... of length B
   const T* tw_n1;     // W_n1^k, k < n1
   double2* spec;
+  int* err;           // sticky device error word
   R inv_n;
 };
 
+#ifndef LSP_R2_NT_C64
+#define LSP_R2_NT_C64 256
+#endif
+#ifndef LSP_R2_MINB
+#define LSP_R2_MINB 3
+#endif
+#ifndef LSP_R2_MINB_C128
+#define LSP_R2_MINB_C128 1
+#endif
+#ifndef LSP_R2_PREFETCH
+#define LSP_R2_PREFETCH 0
+#endif
+// NT threads of 16 elements each per CTA, at least MINB CTAs per SM (register
+// cap); PRE: stage the next tile with bulk asynchronous copies instead of
+// loading it directly.  Measured on the 2^14 x 2^12 lattice (complex64), three
+// 256-thread CTAs per SM with direct loads beat one or two 512-thread CTAs
+// per SM with or without staging: independent CTAs overlap one another's load
+// and transform phases.
 template <typename T> struct R2Cfg;
-template <> struct R2Cfg<float2> { static constexpr int NT = 512, TILE = 8192; };
-template <> struct R2Cfg<double2> { static constexpr int NT = 256, TILE = 4096; };
-
-template <int M1, int M2> struct R2Geo {
-  static constexpr int LA = (M1 + 1) / 2;   // log2 A
-  static constexpr int LB = M1 - LA;        // log2 B
+template <> struct R2Cfg<float2> {
+  static constexpr int NT = LSP_R2_NT_C64, TILE = 16 * NT, MINB = LSP_R2_MINB;
+  static constexpr bool PRE = LSP_R2_PREFETCH != 0;
+};
+template <> struct R2Cfg<double2> {
+  static constexpr int NT = 256, TILE = 4096, MINB = LSP_R2_MINB_C128;
+  static constexpr bool PRE = LSP_R2_PREFETCH != 0;
 };
 
 enum R2Kind { kR2Head = 0, kR2Mid = 1, kR2Tail = 2, kR2RowFwd = 3, kR2A = 4, kR2AInv = 5, kR2B = 6, kR2BFwd = 7 };
 
-template <typename T> __device__ __forceinline__ T g_ld(const T* p) { return __ldcg(p); }
-template <typename T> __device__ __forceinline__ void g_st(T* p, T v) { __stcg(p, v); }
+// Compile-time geometry of one sweep kind: which lines a tile holds and where
+// element i of line b of tile t sits in the state.
+template <typename T, int M1, int M2, int KIND> struct R2Geo {
+  static constexpr int NT = R2Cfg<T>::NT, TILE = R2Cfg<T>::TILE;
+  static constexpr int LA = (M1 + 1) / 2;   // log2 A
+  static constexpr int LB = M1 - LA;        // log2 B
+  static constexpr bool ROW = KIND <= kR2RowFwd;
+  static constexpr bool SWEEP_A = KIND == kR2A || KIND == kR2AInv;
+  static constexpr int LOGL = ROW ? M2 : SWEEP_A ? LB : LA;
+  using G = Line<T, NT, LOGL, ROW>;
+  static constexpr int LOGC = G::LOGC;
+  static_assert(ROW ? LOGC <= M1 : LOGC <= M2, "tile larger than the lattice");
+  // log2 of the element stride along a line
+  static constexpr int ISTRIDE = ROW ? 0 : SWEEP_A ? LA + M2 : M2;
+  static constexpr int PER = ROW ? 1 : 1 << (M2 - LOGC);   // column tiles per outer index
+  static constexpr int NTILES = ROW ? (1 << M1) >> LOGC : PER << (SWEEP_A ? LA : LB);
+  // first element of tile t (line b adds b, or b << M2 for rows)
+  static __device__ __forceinline__ size_t base(int t, int& outer) {
+    if constexpr (ROW) { outer = 0; return (size_t)t << (LOGC + M2); }
+    else {
+      outer = t / PER;
+      const int c0 = (t % PER) << LOGC;
+      return (SWEEP_A ? ((size_t)outer << M2) : ((size_t)outer << (LA + M2))) + c0;
+    }
+  }
+  static __device__ __forceinline__ size_t off(int b, int i) {
+    return ROW ? ((size_t)b << M2) + i : (size_t)b + ((size_t)i << ISTRIDE);
+  }
+  // element (b, i) in the prefetch buffer: rows in natural order, columns i-major
+  static __device__ __forceinline__ int pidx(int b, int i) { return ROW ? (b << M2) + i : (i << LOGC) + b; }
+};
 
-// Rows: contiguous lines kappa2 of length n2; IDFT . P . DFT (head: P . DFT,
-// tail: IDFT . P, row-forward: DFT only).
+// Bulk copies of tile t into the prefetch buffer (all threads issue a share).
 template <typename T, int M1, int M2, int KIND>
-__global__ void __launch_bounds__(R2Cfg<T>::NT) r2_rows(const __grid_constant__ R2Inst<T> I) {
-  constexpr int NT = R2Cfg<T>::NT;
-  using G = Line<T, NT, M2, true>;
-  constexpr int LR1 = G::LOGR1, R1 = G::R1;
-  constexpr bool inv = KIND == kR2Mid || KIND == kR2Tail;
-  constexpr bool fwd = KIND != kR2Tail;
+__device__ __forceinline__ void r2_prefetch(const T* u, int t, T* pre, unsigned long long* mb) {
+  using Geo = R2Geo<T, M1, M2, KIND>;
+  int outer;
+  const T* src = u + Geo::base(t, outer);
+  if constexpr (Geo::ROW) {
+    constexpr int CHUNK = 4096 / (int)sizeof(T);
+    for (int c = threadIdx.x; c < Geo::TILE / CHUNK; c += Geo::NT)
+      bulk_g2s(pre + c * CHUNK, src + c * CHUNK, CHUNK * (unsigned)sizeof(T), mb);
+  } else {
+    constexpr int L = 1 << Geo::LOGL, C = 1 << Geo::LOGC;
+    for (int i = threadIdx.x; i < L; i += Geo::NT)
+      bulk_g2s(pre + i * C, src + ((size_t)i << Geo::ISTRIDE), C * (unsigned)sizeof(T), mb);
+  }
+}
+
+// One sweep.  Each CTA walks its tiles; the next tile's bulk copy is in flight
+// while the current one is transformed.
+//   rows (Head/Mid/Tail/RowFwd): [IDFT_n2, 1/n, P] then DFT_n2 (Tail: no DFT)
+//   A   : DFT_B over b, times W_n1^{a g}      AInv: times conj W_n1^{a g}, IDFT_B
+//   B   : DFT_A, K, IDFT_A                    BFwd: DFT_A, 1/n, to chi order (c128)
+template <typename T, int M1, int M2, int KIND>
+__global__ void __launch_bounds__(R2Cfg<T>::NT, R2Cfg<T>::MINB) r2_sweep(const __grid_constant__ R2Inst<T> I) {
+  using Geo = R2Geo<T, M1, M2, KIND>;
+  using G = typename Geo::G;
+  constexpr int LOGL = Geo::LOGL, LR1 = G::LOGR1, R1 = G::R1, TILE = Geo::TILE;
+  constexpr int LA = Geo::LA, LB = Geo::LB;
+  constexpr unsigned TILE_BYTES = TILE * (unsigned)sizeof(T);
+  // natural-order input: registers hold v[t] = x[j + t L/16] (bm<4>); else the pass-1 pattern
+  constexpr bool nat_in = KIND == kR2Mid || KIND == kR2Tail || KIND == kR2AInv;
   extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long mb;
+  __shared__ int s_fail;
   T* sm = reinterpret_cast<T*>(smraw);
-  const int ntiles = (1 << M1) >> G::LOGC;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int r0 = tile << G::LOGC;
+  T* pre = sm + TILE;
+  const T* tw_line = Geo::ROW ? I.tw_rows : Geo::SWEEP_A ? I.tw_b : I.tw_a;
+
+  constexpr bool PRE = R2Cfg<T>::PRE;
+  int t = blockIdx.x;
+  if (t >= Geo::NTILES) return;
+  unsigned parity = 0;
+  if constexpr (PRE) {
+    if (threadIdx.x == 0) {
+      mbar_init(&mb, 1);
+      s_fail = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&mb, TILE_BYTES);
+    __syncthreads();
+    fence_proxy_async();
+    r2_prefetch<T, M1, M2, KIND>(I.u, t, pre, &mb);
+  }
+  for (; t < Geo::NTILES; t += gridDim.x) {
+    if constexpr (PRE) {
+      if (!wait_prefetch(&mb, parity, I.err)) s_fail = 1;
+      __syncthreads();
+      if (s_fail) return;
+      parity ^= 1u;
+    }
+    int outer;
+    const size_t base = Geo::base(t, outer);
+    // element (b, i) of the tile: from the prefetch buffer, or straight from the state
+    auto ld = [&](int b, int i) { return PRE ? pre[Geo::pidx(b, i)] : ldst(I.u + base + Geo::off(b, i)); };
     T v[16];
-    if constexpr (inv) {
+    if constexpr (nat_in) {
       int b, j; G::template bm<4>(0, b, j);
 #pragma unroll
-      for (int t = 0; t < 16; ++t) v[t] = g_ld(I.u + (((r0 + b) << M2) + j + (t << (M2 - 4))));
-      G::idft(sm, I.tw_rows, v);
+      for (int q = 0; q < 16; ++q) v[q] = ld(b, j + (q << (LOGL - 4)));
     } else {
 #pragma unroll
       for (int q = 0; q < 16 / R1; ++q) {
         int b, j; G::template bm<LR1>(q, b, j);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) v[q * R1 + r] = g_ld(I.u + (((r0 + b) << M2) + j + (r << (M2 - LR1))));
+        for (int r = 0; r < R1; ++r) v[q * R1 + r] = ld(b, j + (r << (LOGL - LR1)));
       }
     }
-    if constexpr (KIND != kR2RowFwd) {
-      const T* P = KIND == kR2Mid ? I.Pf : I.Ph;
+    if constexpr (PRE) {
+      const bool more = t + (int)gridDim.x < Geo::NTILES;
+      if (more && threadIdx.x == 0) mbar_arrive_expect_tx(&mb, TILE_BYTES);
+      __syncthreads();                                  // prefetch buffer free: refill it
+      if (more) {
+        fence_proxy_async();
+        r2_prefetch<T, M1, M2, KIND>(I.u, t + gridDim.x, pre, &mb);
+      }
+    } else {
+      __syncthreads();                                  // previous tile's exchange reads done
+    }
+
+    if constexpr (Geo::ROW) {
+      if constexpr (nat_in) G::idft(sm, tw_line, v);
+      if constexpr (KIND != kR2RowFwd) {
+        const T* P = KIND == kR2Mid ? I.Pf : I.Ph;
+#pragma unroll
+        for (int q = 0; q < 16 / R1; ++q) {
+          int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+          for (int r = 0; r < R1; ++r) {
+            T x = v[q * R1 + r];
+            if constexpr (nat_in) x = cscale(x, I.inv_n);
+            v[q * R1 + r] = apply_phase(x, ldtab(P + base + Geo::off(b, j + (r << (LOGL - LR1)))));
+          }
+        }
+      }
+      if constexpr (KIND != kR2Tail) {
+        G::dft(sm, tw_line, v);
+        int b, j; G::template bm<4>(0, b, j);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) stst(I.u + base + Geo::off(b, j + (q << (LOGL - 4))), v[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16 / R1; ++q) {
+          int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+          for (int r = 0; r < R1; ++r) stst(I.u + base + Geo::off(b, j + (r << (LOGL - LR1))), v[q * R1 + r]);
+        }
+      }
+    } else if constexpr (KIND == kR2A) {
+      G::dft(sm, tw_line, v);
+      int b, j; G::template bm<4>(0, b, j);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int g = j + (q << (LB - 4));
+        stst(I.u + base + Geo::off(b, g), cmul(v[q], __ldg(I.tw_n1 + outer * g)));
+      }
+    } else if constexpr (KIND == kR2AInv) {
+      {
+        int b, j; G::template bm<4>(0, b, j);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], __ldg(I.tw_n1 + outer * (j + (q << (LB - 4)))));
+      }
+      G::idft(sm, tw_line, v);
 #pragma unroll
       for (int q = 0; q < 16 / R1; ++q) {
         int b, j; G::template bm<LR1>(q, b, j);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) {
-          T x = v[q * R1 + r];
-          if constexpr (inv) x = cscale(x, I.inv_n);
-          v[q * R1 + r] = apply_phase(x, __ldcs(P + (((r0 + b) << M2) + j + (r << (M2 - LR1)))));
+        for (int r = 0; r < R1; ++r) stst(I.u + base + Geo::off(b, j + (r << (LOGL - LR1))), v[q * R1 + r]);
+      }
+    } else {
+      G::dft(sm, tw_line, v);
+      int b, j; G::template bm<4>(0, b, j);
+      if constexpr (KIND == kR2BFwd) {
+        // bin chi = (g + B e) n2 + xi2 with g = outer; coefficient = DFT / n
+        const int c0 = (t % Geo::PER) << Geo::LOGC;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int e = j + (q << (LA - 4));
+          T x = cscale(v[q], I.inv_n);
+          I.spec[((size_t)(outer + (e << LB)) << M2) + c0 + b] = make_double2((double)x.x, (double)x.y);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], ldtab(I.K + base + Geo::off(b, j + (q << (LA - 4)))));
+        G::idft(sm, tw_line, v);
+#pragma unroll
+        for (int q = 0; q < 16 / R1; ++q) {
+          int bb, jj; G::template bm<LR1>(q, bb, jj);
+#pragma unroll
+          for (int r = 0; r < R1; ++r) stst(I.u + base + Geo::off(bb, jj + (r << (LOGL - LR1))), v[q * R1 + r]);
         }
       }
     }
-    if constexpr (fwd) {
-      G::dft(sm, I.tw_rows, v);
-      int b, j; G::template bm<4>(0, b, j);
-#pragma unroll
-      for (int t = 0; t < 16; ++t) g_st(I.u + (((r0 + b) << M2) + j + (t << (M2 - 4))), v[t]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) g_st(I.u + (((r0 + b) << M2) + j + (r << (M2 - LR1))), v[q * R1 + r]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Pass A (forward or inverse): lines (a, kappa2), elements b at stride LA n2.
-template <typename T, int M1, int M2, int KIND>
-__global__ void __launch_bounds__(R2Cfg<T>::NT) r2_colA(const __grid_constant__ R2Inst<T> I) {
-  constexpr int NT = R2Cfg<T>::NT;
-  constexpr int LA = R2Geo<M1, M2>::LA, LB = R2Geo<M1, M2>::LB;
-  using G = Line<T, NT, LB, false>;
-  static_assert(G::LOGC <= M2, "tile wider than a row");
-  constexpr int LR1 = G::LOGR1, R1 = G::R1;
-  constexpr int STRIDE = LA + M2;                       // log2 of the element stride
-  extern __shared__ __align__(128) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
-  constexpr int per_a = 1 << (M2 - G::LOGC);            // tiles per a
-  const int ntiles = per_a << LA;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int a = tile / per_a;
-    const int c0 = (tile % per_a) << G::LOGC;
-    const size_t base = ((size_t)a << M2) + c0;
-    T v[16];
-    if constexpr (KIND == kR2A) {
-      // DFT over b (pass-1 pattern), then W_n1^{a g} on the outputs g = j + t LB/16
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) v[q * R1 + r] = g_ld(I.u + base + b + ((size_t)(j + (r << (LB - LR1))) << STRIDE));
-      }
-      G::dft(sm, I.tw_b, v);
-      int b, j; G::template bm<4>(0, b, j);
-#pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int g = j + (t << (LB - 4));
-        g_st(I.u + base + b + ((size_t)g << STRIDE), cmul(v[t], __ldg(I.tw_n1 + a * g)));
-      }
-    } else {
-      int b, j; G::template bm<4>(0, b, j);
-#pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int g = j + (t << (LB - 4));
-        v[t] = cmulc(g_ld(I.u + base + b + ((size_t)g << STRIDE)), __ldg(I.tw_n1 + a * g));
-      }
-      G::idft(sm, I.tw_b, v);
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int bb, jj; G::template bm<LR1>(q, bb, jj);
-#pragma unroll
-        for (int r = 0; r < R1; ++r)
-          g_st(I.u + base + bb + ((size_t)(jj + (r << (LB - LR1))) << STRIDE), v[q * R1 + r]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Pass B: lines (g, kappa2), elements a at stride n2: DFT . K . IDFT (or DFT and
-// spectral output in chi order).
-template <typename T, int M1, int M2, int KIND>
-__global__ void __launch_bounds__(R2Cfg<T>::NT) r2_colB(const __grid_constant__ R2Inst<T> I) {
-  constexpr int NT = R2Cfg<T>::NT;
-  constexpr int LA = R2Geo<M1, M2>::LA, LB = R2Geo<M1, M2>::LB;
-  using G = Line<T, NT, LA, false>;
-  static_assert(G::LOGC <= M2, "tile wider than a row");
-  constexpr int LR1 = G::LOGR1, R1 = G::R1;
-  extern __shared__ __align__(128) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
-  constexpr int per_g = 1 << (M2 - G::LOGC);
-  const int ntiles = per_g << LB;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int g = tile / per_g;
-    const int c0 = (tile % per_g) << G::LOGC;
-    const size_t base = ((size_t)g << (LA + M2)) + c0;  // element a of line (g, c) at base + c + a n2
-    T v[16];
-#pragma unroll
-    for (int q = 0; q < 16 / R1; ++q) {
-      int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-      for (int r = 0; r < R1; ++r) v[q * R1 + r] = g_ld(I.u + base + b + ((size_t)(j + (r << (LA - LR1))) << M2));
-    }
-    G::dft(sm, I.tw_a, v);
-    int b, j; G::template bm<4>(0, b, j);
-    if constexpr (KIND == kR2BFwd) {
-      // bin chi = (g + LB e) n2 + xi2, coefficient = DFT / n
-#pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int e = j + (t << (LA - 4));
-        T x = cscale(v[t], I.inv_n);
-        I.spec[((size_t)(g + (e << LB)) << M2) + c0 + b] = make_double2((double)x.x, (double)x.y);
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int e = j + (t << (LA - 4));
-        v[t] = apply_phase(v[t], __ldcs(I.K + base + b + ((size_t)e << M2)));
-      }
-      G::idft(sm, I.tw_a, v);
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int bb, jj; G::template bm<LR1>(q, bb, jj);
-#pragma unroll
-        for (int r = 0; r < R1; ++r)
-          g_st(I.u + base + bb + ((size_t)(jj + (r << (LA - LR1))) << M2), v[q * R1 + r]);
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -221,18 +271,22 @@ __global__ void __launch_bounds__(R2Cfg<T>::NT) r2_colB(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 struct R2Kernels {
   const void* k[8] = {};
+  int ntiles[3] = {};   // tiles of a row sweep, an A sweep, a B sweep
 };
 
 template <typename T, int M1, int M2> static R2Kernels r2_kernels() {
   R2Kernels K;
-  K.k[kR2Head] = (const void*)r2_rows<T, M1, M2, kR2Head>;
-  K.k[kR2Mid] = (const void*)r2_rows<T, M1, M2, kR2Mid>;
-  K.k[kR2Tail] = (const void*)r2_rows<T, M1, M2, kR2Tail>;
-  K.k[kR2RowFwd] = (const void*)r2_rows<T, M1, M2, kR2RowFwd>;
-  K.k[kR2A] = (const void*)r2_colA<T, M1, M2, kR2A>;
-  K.k[kR2AInv] = (const void*)r2_colA<T, M1, M2, kR2AInv>;
-  K.k[kR2B] = (const void*)r2_colB<T, M1, M2, kR2B>;
-  K.k[kR2BFwd] = (const void*)r2_colB<T, M1, M2, kR2BFwd>;
+  K.k[kR2Head] = (const void*)r2_sweep<T, M1, M2, kR2Head>;
+  K.k[kR2Mid] = (const void*)r2_sweep<T, M1, M2, kR2Mid>;
+  K.k[kR2Tail] = (const void*)r2_sweep<T, M1, M2, kR2Tail>;
+  K.k[kR2RowFwd] = (const void*)r2_sweep<T, M1, M2, kR2RowFwd>;
+  K.k[kR2A] = (const void*)r2_sweep<T, M1, M2, kR2A>;
+  K.k[kR2AInv] = (const void*)r2_sweep<T, M1, M2, kR2AInv>;
+  K.k[kR2B] = (const void*)r2_sweep<T, M1, M2, kR2B>;
+  K.k[kR2BFwd] = (const void*)r2_sweep<T, M1, M2, kR2BFwd>;
+  K.ntiles[0] = R2Geo<T, M1, M2, kR2Mid>::NTILES;
+  K.ntiles[1] = R2Geo<T, M1, M2, kR2A>::NTILES;
+  K.ntiles[2] = R2Geo<T, M1, M2, kR2B>::NTILES;
   return K;
 }
 
@@ -262,6 +316,7 @@ template <typename T> static R2Inst<T> r2_inst(lsp_plan p, void* state) {
   I.tw_b = tw + p->twr_entries + p->twa_entries;
   I.tw_n1 = (const T*)p->tw_line;
   I.spec = (double2*)p->stage;
+  I.err = p->err;
   I.inv_n = (decltype(I.inv_n))(1.0 / (double)p->ntot);
   return I;
 }
@@ -286,50 +341,45 @@ static int r2_grid(const void* fn, int nt, size_t smem, int* grid) {
   return LSP_OK;
 }
 
+// Dynamic shared memory of a sweep: exchange buffer (and prefetch buffer).
+template <typename T> constexpr size_t r2_smem() {
+  return (R2Cfg<T>::PRE ? 2 : 1) * (size_t)R2Cfg<T>::TILE * sizeof(T);
+}
+
 template <typename T> static int r2_launch(const void* fn, const R2Inst<T>& I, int ntiles, cudaStream_t s) {
   constexpr int NT = R2Cfg<T>::NT;
-  const size_t smem = (size_t)R2Cfg<T>::TILE * sizeof(T);
   int grid = 0;
-  int rc = r2_grid(fn, NT, smem, &grid);
+  int rc = r2_grid(fn, NT, r2_smem<T>(), &grid);
   if (rc) return rc;
   grid = std::max(1, std::min(ntiles, grid));
   void* args[] = {(void*)&I};
-  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s));
+  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, r2_smem<T>(), s));
   return LSP_OK;
 }
 
 template <typename T> static int r2_steps_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
   R2Kernels K;
-  const int m1 = p->logN1, m2 = p->logN2;
-  if (!r2_lookup<T>(m1, m2, &K)) return LSP_ERR_UNSUPPORTED;
-  R2Inst<T> I = r2_inst<T>(p, state);
-  const int la = (m1 + 1) / 2, lb = m1 - la;
-  const int logTile = R2Cfg<T>::TILE == 8192 ? 13 : 12;
-  const int rows_tiles = (1 << m1) >> (logTile - m2);
-  const int a_tiles = (1 << (m2 - (logTile - lb))) << la;
-  const int b_tiles = (1 << (m2 - (logTile - la))) << lb;
+  if (!r2_lookup<T>(p->logN1, p->logN2, &K)) return LSP_ERR_UNSUPPORTED;
+  const R2Inst<T> I = r2_inst<T>(p, state);
   int rc = LSP_OK;
   for (int64_t st = 0; st < nsteps && !rc; ++st) {
-    rc = r2_launch<T>(K.k[st == 0 ? kR2Head : kR2Mid], I, rows_tiles, s);
-    if (!rc) rc = r2_launch<T>(K.k[kR2A], I, a_tiles, s);
-    if (!rc) rc = r2_launch<T>(K.k[kR2B], I, b_tiles, s);
-    if (!rc) rc = r2_launch<T>(K.k[kR2AInv], I, a_tiles, s);
+    rc = r2_launch<T>(K.k[st == 0 ? kR2Head : kR2Mid], I, K.ntiles[0], s);
+    if (!rc) rc = r2_launch<T>(K.k[kR2A], I, K.ntiles[1], s);
+    if (!rc) rc = r2_launch<T>(K.k[kR2B], I, K.ntiles[2], s);
+    if (!rc) rc = r2_launch<T>(K.k[kR2AInv], I, K.ntiles[1], s);
   }
-  if (!rc) rc = r2_launch<T>(K.k[kR2Tail], I, rows_tiles, s);
+  if (!rc) rc = r2_launch<T>(K.k[kR2Tail], I, K.ntiles[0], s);
   return rc;
 }
 
 template <typename T> static int r2_spectral_impl(lsp_plan p, cudaStream_t s) {
   R2Kernels K;
-  const int m1 = p->logN1, m2 = p->logN2;
-  if (!r2_lookup<T>(m1, m2, &K)) return LSP_ERR_UNSUPPORTED;
+  if (!r2_lookup<T>(p->logN1, p->logN2, &K)) return LSP_ERR_UNSUPPORTED;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->work, p->u, (size_t)p->ntot * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  R2Inst<T> I = r2_inst<T>(p, p->work);
-  const int la = (m1 + 1) / 2, lb = m1 - la;
-  const int logTile = R2Cfg<T>::TILE == 8192 ? 13 : 12;
-  int rc = r2_launch<T>(K.k[kR2RowFwd], I, (1 << m1) >> (logTile - m2), s);
-  if (!rc) rc = r2_launch<T>(K.k[kR2A], I, (1 << (m2 - (logTile - lb))) << la, s);
-  if (!rc) rc = r2_launch<T>(K.k[kR2BFwd], I, (1 << (m2 - (logTile - la))) << lb, s);
+  const R2Inst<T> I = r2_inst<T>(p, p->work);
+  int rc = r2_launch<T>(K.k[kR2RowFwd], I, K.ntiles[0], s);
+  if (!rc) rc = r2_launch<T>(K.k[kR2A], I, K.ntiles[1], s);
+  if (!rc) rc = r2_launch<T>(K.k[kR2BFwd], I, K.ntiles[2], s);
   return rc;
 }
 
