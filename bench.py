@@ -395,7 +395,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,            # build_klut, build_tables, head, persistent, tail
         }
         print(json.dumps(out))
     plan.destroy()
