@@ -45,6 +45,9 @@ template <typename T> struct R2Inst {
 #ifndef LSP_R2_MINB
 #define LSP_R2_MINB 3
 #endif
+#ifndef LSP_R2_MINB_2T
+#define LSP_R2_MINB_2T 3
+#endif
 #ifndef LSP_R2_MINB_C128
 #define LSP_R2_MINB_C128 1
 #endif
@@ -59,11 +62,11 @@ template <typename T> struct R2Inst {
 // and transform phases.
 template <typename T> struct R2Cfg;
 template <> struct R2Cfg<float2> {
-  static constexpr int NT = LSP_R2_NT_C64, TILE = 16 * NT, MINB = LSP_R2_MINB;
+  static constexpr int NT = LSP_R2_NT_C64, TILE = 16 * NT, MINB = LSP_R2_MINB, MINB_2T = LSP_R2_MINB_2T;
   static constexpr bool PRE = LSP_R2_PREFETCH != 0;
 };
 template <> struct R2Cfg<double2> {
-  static constexpr int NT = 256, TILE = 4096, MINB = LSP_R2_MINB_C128;
+  static constexpr int NT = 256, TILE = 4096, MINB = LSP_R2_MINB_C128, MINB_2T = LSP_R2_MINB_C128;
   static constexpr bool PRE = LSP_R2_PREFETCH != 0;
 };
 
@@ -124,7 +127,8 @@ __device__ __forceinline__ void r2_prefetch(const T* u, int t, T* pre, unsigned 
 //   A   : DFT_B over b, times W_n1^{a g}      AInv: times conj W_n1^{a g}, IDFT_B
 //   B   : DFT_A, K, IDFT_A                    BFwd: DFT_A, 1/n, to chi order (c128)
 template <typename T, int M1, int M2, int KIND>
-__global__ void __launch_bounds__(R2Cfg<T>::NT, R2Cfg<T>::MINB) r2_sweep(const __grid_constant__ R2Inst<T> I) {
+__global__ void __launch_bounds__(R2Cfg<T>::NT, (KIND == kR2Mid || KIND == kR2B) ? R2Cfg<T>::MINB_2T : R2Cfg<T>::MINB)
+    r2_sweep(const __grid_constant__ R2Inst<T> I) {
   using Geo = R2Geo<T, M1, M2, KIND>;
   using G = typename Geo::G;
   constexpr int LOGL = Geo::LOGL, LR1 = G::LOGR1, R1 = G::R1, TILE = Geo::TILE;
