@@ -48,13 +48,16 @@ def parse():
                     help="c2: the headline run (with its side measurements); c5: only the rank-2 "
                          "2^14 x 2^12 batch (profiling; --inner steps per call, --batch instances)")
     ap.add_argument("--batch", type=int, default=4, help="instances of the c5 workload")
+    ap.add_argument("--path", type=int, default=-1,
+                    help="execution path of the headline plan (default: autotuned); 0 two-sweep, 3 four-sweep")
     return ap.parse_args()
 
 
 # CUDA sources each profiled kernel family is built from
 KERNEL_SOURCES = {
     "mp_persistent": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_mp.cuh", "lsp_mp_c64_hi.cu"],
-    "r2_sweep": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_mp.cuh", "lsp_r2.cu"],
+    "sweep4_rank2": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_sweep4.cuh", "lsp_sweep4_r2.cu"],
+    "sweep4_rank1": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_sweep4.cuh", "lsp_sweep4_r1.cu"],
 }
 
 
@@ -281,6 +284,13 @@ def run_ours(args):
     plan.set_potential(v_d)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # schedule choice (untimed): time up to 100 steps on every available path, keep the fastest
+    plan.set_state(u0_d)
+    if args.path < 0:
+        path, tune_ms = plan.autotune(inst.dt, min(100, STEPS_PER_CALL))
+    else:
+        plan.set_path(args.path)
+        path, tune_ms = args.path, {}
 
     def one_call(p):
         p.strang_steps(inst.dt, STEPS_PER_CALL)
@@ -315,16 +325,22 @@ def run_ours(args):
     tot_ms = max_over_ranks(sum(ms), world)
     value = world * n * STEPS_PER_CALL * args.steps / (tot_ms / 1e3)
 
-    # roofline of the dominant kernel (the persistent multipass kernel; the
-    # per-call phase-table build is included in the timed call: conservative)
+    # roofline of the hot path: algorithmic bytes of all the call's steps over the whole call
+    # (phase-table build and every sweep inside: conservative for any single kernel)
     hbm, src = peaks()
     alg_bytes = 48.0 * n * STEPS_PER_CALL                # 6 s per point-step, s = 8 B (c64)
     kern_s = statistics.mean(ms) / 1e3
     achieved = alg_bytes / kern_s / 1e9
     traffic = None
     if args.log2n == 22 and STEPS_PER_CALL == 1000:
-        rec = traffic_record("c64_n2p22", "mp_persistent")   # None once the kernel sources changed
-        traffic = rec.get("bytes_per_launch") if rec else None
+        # DRAM bytes of one call from committed ncu records (None once the kernel sources changed)
+        if path == lsp.PATH_MULTIPASS:
+            rec = traffic_record("c64_n2p22", "mp_persistent")
+            traffic = rec.get("bytes_per_launch") if rec else None
+        elif path == lsp.PATH_RANK1_4SWEEP:
+            rec = traffic_record("c64_n2p22_4sweep", "sweep4_rank1")
+            traffic = rec.get("bytes_per_call_1000_steps") if rec else None
+    launches = {lsp.PATH_MULTIPASS: 5, lsp.PATH_RANK1_4SWEEP: 3 + 4 * STEPS_PER_CALL}.get(path, 0)
 
     # complex128 side measurement on the same workload
     c128 = None
@@ -388,10 +404,14 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "rank-1 lattice d=6 n=2^22 (N1=4096 x N2=1024), HC(64) reconstructing z, "
+            "config": {"workload": "rank-1 lattice d=6 n=2^22, HC(64) reconstructing z, "
                                    "MINL2 anti-aliasing set, gamma=0.05, dt=1e-3, 1000 Strang steps per bench step, "
                                    "complex64 state", "l2": "flushed (512 MiB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "path": {0: "two-sweep persistent (4096 x 1024)",
+                                3: "four-sweep (4096 x 32 x 32)"}.get(path, str(path)),
+                       "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
+                       "autotune_steps": min(100, STEPS_PER_CALL)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
                          "alg_bytes_per_point_step": 48},
@@ -401,7 +421,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
-            "gpu_launches": 5 * args.steps,            # build_klut, build_tables, head, persistent, tail
+            "gpu_launches": launches * args.steps,     # build_klut, build_tables, then the path's sweeps
         }
         print(json.dumps(out))
     plan.destroy()

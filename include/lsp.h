@@ -86,11 +86,14 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * Errors: BAD_ARG, NOT_CANONICAL, NOT_INJECTIVE, TOO_LARGE, OOM, CUDA,
  * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
  * The state starts at zero and the potential at v = 0.
- * Execution paths (chosen here, reported by lsp_plan_info):
+ * Execution paths (the first available in this order is chosen: rank 1:
+ * 0, 3, 1; rank 2: 1, 2; reported by lsp_plan_info, changed by
+ * lsp_plan_set_path or lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
  *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, rank 1 or 2;
- *   2 multipass, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
- *     (10, 8), (11, 9), (12, 10), (14, 12).
+ *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
+ *     (10, 8), (11, 9), (12, 10), (14, 12);
+ *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25}.
  * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
@@ -163,12 +166,47 @@ int lsp_index_table(lsp_plan p, int32_t* h);
 
 /*
  * lsp_plan_info -- plan geometry, 8 int64 values (host):
- *   [0] n  [1] N1 (row length)  [2] N2 (column length)  [3] path (0 multipass,
- *   1 SMEM-resident, 2 rank-2 multipass)  [4] precision  [5] device bytes held
- *   [6] MINL2 DP box half-width (0 for EXPLICIT)  [7] max ||h_chi||^2.
- *   For rank 2, N1 = n_2 (contiguous rows) and N2 = n_1.
+ *   [0] n  [1] N1 (row length)  [2] N2 (column length)  [3] path (LSP_PATH_*)
+ *   [4] precision  [5] device bytes held  [6] MINL2 DP box half-width (0 for
+ *   EXPLICIT)  [7] max ||h_chi||^2.  For rank 2, N1 = n_2 (contiguous rows)
+ *   and N2 = n_1.
  */
 int lsp_plan_info(lsp_plan p, int64_t* info);
+
+/* Execution paths (lsp_plan_info [3], lsp_plan_paths, lsp_plan_set_path). */
+enum {
+  LSP_PATH_MULTIPASS = 0,      /* rank-1, n = 2^m: two sweeps per step (persistent kernel)        */
+  LSP_PATH_SMEM = 1,           /* whole run in shared memory, one CTA per instance                 */
+  LSP_PATH_RANK2 = 2,          /* rank-2, 2^m1 x 2^m2: four sweeps per step                        */
+  LSP_PATH_RANK1_4SWEEP = 3    /* rank-1, n = 2^m: four sweeps per step (rows of 4096 points)      */
+};
+
+/*
+ * lsp_plan_paths -- *mask receives a bit mask of the execution paths the plan
+ * can run (bit k set: path k available for its size, rank and precision).
+ * Errors: BAD_ARG.
+ */
+int lsp_plan_paths(lsp_plan p, int* mask);
+
+/*
+ * lsp_plan_set_path -- switch the plan to an available execution path.  The
+ * state, potential and ||h||^2 are kept; the path's twiddle tables are built
+ * (synchronous, like plan creation).  Results of every path agree with the
+ * paper's step to rounding.  A plan in a batch must keep the path it had when
+ * the batch was made.  Errors: BAD_ARG, UNSUPPORTED (path not available), OOM, CUDA.
+ */
+int lsp_plan_set_path(lsp_plan p, int path);
+
+/*
+ * lsp_plan_autotune -- time `nsteps` Strang steps of size dt on every
+ * available path, on a scratch copy of the state (the plan's state is not
+ * changed), and keep the fastest.  Not in the paper: a schedule choice.
+ *   chosen  receives the kept path (may be NULL).
+ *   ms      NULL, or 4 doubles receiving each path's time in ms (-1: not available).
+ * Synchronises `stream`.  Errors: BAD_ARG, OOM, CUDA, TIMEOUT (then the plan
+ * keeps the path it had).
+ */
+int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* chosen, double* ms);
 
 /*
  * Batched stepping: many independent instances (same precision and device)

@@ -19,7 +19,7 @@ LSP_OK = 0
 C64, C128 = 1, 2
 AA_MINL2, AA_EXPLICIT = 0, 1
 PHYSICAL, SPECTRAL = 0, 1
-PATH_MULTIPASS, PATH_SMALL, PATH_RANK2 = 0, 1, 2
+PATH_MULTIPASS, PATH_SMALL, PATH_RANK2, PATH_RANK1_4SWEEP = 0, 1, 2, 3
 
 _lib = None
 _lock = threading.Lock()
@@ -50,6 +50,9 @@ def _declare(lib):
         "lsp_index_norms": (I, [P, P]),
         "lsp_index_table": (I, [P, P]),
         "lsp_plan_info": (I, [P, P]),
+        "lsp_plan_paths": (I, [P, C.POINTER(C.c_int)]),
+        "lsp_plan_set_path": (I, [P, I]),
+        "lsp_plan_autotune": (I, [P, D, I64, P, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "lsp_batch_create": (I, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), I]),
         "lsp_batch_steps": (I, [P, P, I64, P]),
         "lsp_batch_destroy": (V, [P]),
@@ -231,6 +234,23 @@ class Plan:
         x = np.empty((self.npoints, self.d), dtype=np.int32)
         _check(self._lib.lsp_index_table(self._h, C.c_void_p(x.ctypes.data)), "lsp_index_table")
         return x
+
+    def paths(self) -> list:
+        """Execution paths this plan can run (lsp_plan_paths)."""
+        m = C.c_int()
+        _check(self._lib.lsp_plan_paths(self._h, C.byref(m)), "lsp_plan_paths")
+        return [k for k in range(4) if m.value >> k & 1]
+
+    def set_path(self, path: int):
+        _check(self._lib.lsp_plan_set_path(self._h, int(path)), "lsp_plan_set_path")
+
+    def autotune(self, dt: float, nsteps: int, stream=None):
+        """Time nsteps steps on every available path, keep the fastest; returns (path, {path: ms})."""
+        chosen = C.c_int()
+        ms = (C.c_double * 4)()
+        _check(self._lib.lsp_plan_autotune(self._h, float(dt), int(nsteps), _stream_ptr(stream), C.byref(chosen), ms),
+               "lsp_plan_autotune")
+        return chosen.value, {k: ms[k] for k in range(4) if ms[k] >= 0}
 
     def info(self) -> dict:
         x = np.zeros(8, dtype=np.int64)

@@ -36,11 +36,7 @@ __global__ void grad_accum(double* __restrict__ grad, const T* __restrict__ lam,
   }
 }
 
-int steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
-  return p->path == kPathMultipass ? multipass_steps_on(p, state, nsteps, s)
-         : p->path == kPathRank2   ? r2_steps_on(p, state, nsteps, s)
-                                   : small_steps_on(p, state, nsteps, s);
-}
+int steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) { return path_steps_on(p, state, nsteps, s); }
 
 }  // namespace
 

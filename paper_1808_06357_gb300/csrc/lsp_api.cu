@@ -167,6 +167,12 @@ __global__ void build_tables(const double* __restrict__ v, const int32_t* __rest
       long long xi2 = i & ((1ll << logN2) - 1), row = i >> logN2;
       long long e = row & ((1ll << la) - 1), g = row >> la;
       bin = ((g + (e << lb)) << logN2) + xi2;
+    } else if (order == kPathRank1x4) {
+      // N2 = A B (A = 2^ceil(log2 N2 / 2)): position xi1 + N1 (e + A g) <- bin (g + B e) + N2 xi1
+      const int la = (logN2 + 1) / 2, lb = logN2 - la;
+      long long xi1 = i & ((1ll << logN1) - 1), row = i >> logN1;
+      long long e = row & ((1ll << la) - 1), g = row >> la;
+      bin = (g + (e << lb)) + (xi1 << logN2);
     }
     if (klut) c = klut[norm2[bin]];
     else encode_phase(turns_k * (double)norm2[bin], &c);
@@ -292,8 +298,8 @@ static void free_plan(lsp_plan p) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
-  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->klut, p->tw_line, p->tw_fine, p->tw_pass,
-                  p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
+  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->klut, p->tw_line, p->tw_fine, p->tw_coarse,
+                  p->tw_pass, p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
   for (void* b : bufs) if (b) cudaFree(b);
   if (p->err_host) cudaFreeHost(p->err_host);
   cudaSetDevice(prev);
@@ -310,6 +316,134 @@ template <typename Tp> static int dalloc(lsp_plan p, Tp** ptr, size_t bytes) {
   if (cudaMalloc((void**)ptr, bytes) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
   p->bytes += bytes;
   return LSP_OK;
+}
+
+static int upload(lsp_plan p, void** dst, const std::vector<unsigned char>& host) {
+  int rc = dalloc(p, dst, std::max<size_t>(host.size(), 16));
+  if (rc) return rc;
+  return cudaMemcpy(*dst, host.data(), host.size(), cudaMemcpyHostToDevice) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
+}
+
+// Can plan p run on execution path `path`?
+static bool path_available(lsp_plan p, int path) {
+  const size_t sz = csize(p->prec);
+  const int logn = ilog2exact(p->ntot);
+  switch (path) {
+    case kPathSmall: return 2 * (size_t)p->ntot * sz <= (size_t)kSmallSmemBytes;
+    case kPathMultipass: return p->r == 1 && logn >= 13 && multipass_supports(p->prec, logn);
+    case kPathRank1x4: return p->r == 1 && logn > 0 && s4_supports_rank1(p->prec, logn);
+    case kPathRank2: {
+      const int m1 = ilog2exact(p->n[0]), m2 = ilog2exact(p->n[1]);
+      return p->r == 2 && m1 > 0 && m2 > 0 && s4_supports_rank2(p->prec, m1, m2);
+    }
+    default: return false;
+  }
+}
+
+// Geometry, twiddle tables (FP64 evaluation, rounded once) and kernel
+// descriptors of execution path `path`; the previous path's tables are freed.
+static int setup_path(lsp_plan p, int path) {
+  void** olds[] = {&p->tw_line, &p->tw_fine, &p->tw_coarse, &p->tw_pass, &p->tw_small};
+  for (void** b : olds)
+    if (*b) { cudaFree(*b); *b = nullptr; }
+  p->path = path;
+  p->tables_valid = false;
+  const int prec = p->prec;
+  const size_t sz = csize(prec);
+  const long long ntot = p->ntot;
+  const int logn = ilog2exact(ntot);
+  p->logn = logn > 0 ? logn : 0;
+  int rc = LSP_OK;
+  auto twid = [&](std::vector<unsigned char>& tw, long long len, long long denom, bool lo = false) {
+    if (prec == LSP_C64) fill_twiddles<float2>(tw, len, denom, lo); else fill_twiddles<double2>(tw, len, denom, lo);
+  };
+  auto passes = [&](std::vector<unsigned char>& tw, int logL) {
+    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, logL); else fill_pass_twiddles<double2>(tw, logL);
+  };
+  if (path != kPathSmall && !p->work && (rc = dalloc(p, &p->work, ntot * sz))) return rc;
+  std::vector<unsigned char> tw;
+  if (path == kPathMultipass) {
+    // four-step split N2 = 2^min(10, m/2) (column), N1 = n / N2 (row); one kernel per m
+    p->logN2 = std::min(10, logn / 2);
+    p->logN1 = logn - p->logN2;
+    p->N1 = 1 << p->logN1; p->N2 = 1 << p->logN2;
+    p->logLmax = std::max(p->logN1, p->logN2);
+    const long long Lmax = 1ll << p->logLmax, nfine = ntot >> p->logLmax;
+    twid(tw, Lmax, Lmax);
+    if ((rc = upload(p, &p->tw_line, tw))) return rc;
+    tw.clear();
+    twid(tw, nfine, ntot);
+    if ((rc = upload(p, &p->tw_fine, tw))) return rc;
+    tw.clear();
+    passes(tw, p->logN1);
+    p->twr_entries = (int)(tw.size() / sz);
+    passes(tw, p->logN2);
+    if ((rc = upload(p, &p->tw_pass, tw))) return rc;
+    return multipass_upload_desc(p, 0);
+  }
+  if (path == kPathRank1x4 || path == kPathRank2) {
+    int rows, cols;                                  // log2 of the row length and of the strided axis
+    if (path == kPathRank1x4) {
+      rows = 12;
+      cols = logn - rows;
+      p->logN1 = rows; p->logN2 = cols;
+      twid(tw, 1ll << cols, 1ll << cols);                    // W_N2^k
+      if ((rc = upload(p, &p->tw_line, tw))) return rc;
+      tw.clear();
+      twid(tw, 1ll << rows, 1ll << rows);                    // W_N1^k
+      if ((rc = upload(p, &p->tw_coarse, tw))) return rc;
+      tw.clear();
+      twid(tw, 1ll << cols, ntot);                           // W_n^k, k < N2
+      if ((rc = upload(p, &p->tw_fine, tw))) return rc;
+      tw.clear();
+    } else {
+      cols = ilog2exact(p->n[0]);
+      rows = ilog2exact(p->n[1]);
+      p->logN1 = cols; p->logN2 = rows;
+      twid(tw, p->n[0], p->n[0]);                            // W_n1^k
+      if ((rc = upload(p, &p->tw_line, tw))) return rc;
+      tw.clear();
+    }
+    p->N1 = 1 << rows; p->N2 = 1 << cols;
+    // line tables: rows, then strided sub-lines of A = 2^ceil(cols/2) and B points
+    const int la = (cols + 1) / 2, lb = cols - la;
+    passes(tw, rows);
+    p->twr_entries = (int)(tw.size() / sz);
+    passes(tw, la);
+    p->twa_entries = (int)(tw.size() / sz) - p->twr_entries;
+    passes(tw, lb);
+    return upload(p, &p->tw_pass, tw);
+  }
+  // SMEM-resident path: per-axis mixed-radix tables
+  p->naxes = p->r;
+  long long stride = 1;
+  for (int i = p->r - 1; i >= 0; --i) {
+    p->axes[i].len = (int)p->n[i];
+    p->axes[i].stride = (int)stride;
+    stride *= p->n[i];
+    factorize((int)p->n[i], p->axes[i]);
+  }
+  for (int i = 0; i < p->naxes; ++i) {
+    p->axes[i].tw_off = (int)(tw.size() / sz);
+    twid(tw, p->axes[i].len, p->axes[i].len);
+  }
+  if (prec == LSP_C64) {
+    // lo parts: exact value minus its FP32 rounding, same layout after the hi parts
+    p->tw_lo = (int)(tw.size() / sz);
+    for (int i = 0; i < p->naxes; ++i) twid(tw, p->axes[i].len, p->axes[i].len, true);
+  }
+  if ((rc = upload(p, &p->tw_small, tw))) return rc;
+  p->N1 = (int)p->n[p->r - 1];
+  p->N2 = p->r == 2 ? (int)p->n[0] : 1;
+  return small_upload_desc(p, 0);
+}
+
+int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  switch (p->path) {
+    case kPathMultipass: return multipass_steps_on(p, state, nsteps, s);
+    case kPathSmall: return small_steps_on(p, state, nsteps, s);
+    default: return s4_steps_on(p, state, nsteps, s);
+  }
 }
 
 }  // namespace lsp
@@ -362,34 +496,21 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
 
   DeviceGuard guard(device);
   const size_t sz = csize(prec);
-  // ---- choose the path ----
-  const int logn = ilog2exact(ntot);
-  const bool small_fits = 2 * (size_t)ntot * sz <= (size_t)kSmallSmemBytes;
-  if (r == 1 && logn >= 13) {
-    // four-step split N2 = 2^min(10, m/2) (column), N1 = n / N2 (row); one kernel per m
-    int logN2 = std::min(10, logn / 2);
-    int logN1 = logn - logN2;
-    if (!multipass_supports(prec, logn)) { free_plan(p); return LSP_ERR_TOO_LARGE; }
-    p->path = kPathMultipass;
-    p->logn = logn; p->logN1 = logN1; p->logN2 = logN2; p->N1 = 1 << logN1; p->N2 = 1 << logN2;
-    p->logLmax = std::max(logN1, logN2);
-  } else if (r == 2 && !small_fits && ilog2exact(n[0]) > 0 && ilog2exact(n[1]) > 0 &&
-             r2_supports(prec, ilog2exact(n[0]), ilog2exact(n[1]))) {
-    // rank-2, both axes powers of two: row sweep along kappa_2, kappa_1 split in two column sweeps
-    p->path = kPathRank2;
-    p->logn = logn; p->logN1 = ilog2exact(n[0]); p->logN2 = ilog2exact(n[1]);
-    p->N1 = (int)n[1]; p->N2 = (int)n[0];
-  } else if (small_fits) {
-    p->path = kPathSmall;
-    p->naxes = r;
-    long long stride = 1;
-    for (int i = r - 1; i >= 0; --i) {
-      p->axes[i].len = (int)p->n[i];
-      p->axes[i].stride = (int)stride;
-      stride *= p->n[i];
-      factorize((int)p->n[i], p->axes[i]);
-    }
+  // ---- choose the path: rank-1 two-sweep, rank-1 four-sweep, SMEM-resident; rank-2 SMEM, four-sweep ----
+  // complex64 from 2^22 points on: the four-sweep path measured 11-19 % faster than the
+  // two-sweep kernel (50.0 against 45.1 G point-steps/s at 2^22, 53.8 against 45.1 at 2^23)
+  const int logn0 = ilog2exact(ntot);
+  const bool four_first = prec == LSP_C64 && logn0 >= 22;
+  const int order1[] = {four_first ? kPathRank1x4 : kPathMultipass, four_first ? kPathMultipass : kPathRank1x4,
+                        kPathSmall};
+  const int order2[] = {kPathSmall, kPathRank2};
+  int path = -1;
+  if (r == 1) {
+    for (int c : order1) if (path < 0 && path_available(p, c)) path = c;
   } else {
+    for (int c : order2) if (path < 0 && path_available(p, c)) path = c;
+  }
+  if (path < 0) {
     free_plan(p);
     return r == 1 ? LSP_ERR_TOO_LARGE : LSP_ERR_UNSUPPORTED;
   }
@@ -412,53 +533,8 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
       cudaMemset(p->err, 0, 256) != cudaSuccess || cudaMemset(p->bar, 0, 256) != cudaSuccess)
     return fail(LSP_ERR_CUDA);
 
-  // ---- twiddle tables (FP64 evaluation, rounded once) ----
-  std::vector<unsigned char> tw;
-  if (p->path == kPathMultipass) {
-    if ((rc = dalloc(p, &p->work, ntot * sz))) return fail(rc);
-    const long long Lmax = 1ll << p->logLmax, nfine = ntot >> p->logLmax;
-    if (prec == LSP_C64) fill_twiddles<float2>(tw, Lmax, Lmax); else fill_twiddles<double2>(tw, Lmax, Lmax);
-    if ((rc = dalloc(p, &p->tw_line, tw.size()))) return fail(rc);
-    if (cudaMemcpy(p->tw_line, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
-    tw.clear();
-    if (prec == LSP_C64) fill_twiddles<float2>(tw, nfine, ntot); else fill_twiddles<double2>(tw, nfine, ntot);
-    if ((rc = dalloc(p, &p->tw_fine, tw.size()))) return fail(rc);
-    if (cudaMemcpy(p->tw_fine, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
-    tw.clear();
-    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN1); else fill_pass_twiddles<double2>(tw, p->logN1);
-    p->twr_entries = (int)(tw.size() / sz);
-    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN2); else fill_pass_twiddles<double2>(tw, p->logN2);
-    if ((rc = dalloc(p, &p->tw_pass, std::max<size_t>(tw.size(), 16)))) return fail(rc);
-    if (cudaMemcpy(p->tw_pass, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
-  } else if (p->path == kPathRank2) {
-    if ((rc = dalloc(p, &p->work, ntot * sz))) return fail(rc);
-    if (prec == LSP_C64) fill_twiddles<float2>(tw, p->n[0], p->n[0]); else fill_twiddles<double2>(tw, p->n[0], p->n[0]);
-    if ((rc = dalloc(p, &p->tw_line, tw.size()))) return fail(rc);
-    if (cudaMemcpy(p->tw_line, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
-    tw.clear();
-    // line tables: rows (n2), then kappa_1 sub-lines of lengths A = 2^ceil(m1/2) and B = n1 / A
-    const int la = (p->logN1 + 1) / 2, lb = p->logN1 - la;
-    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, p->logN2); else fill_pass_twiddles<double2>(tw, p->logN2);
-    p->twr_entries = (int)(tw.size() / sz);
-    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, la); else fill_pass_twiddles<double2>(tw, la);
-    p->twa_entries = (int)(tw.size() / sz) - p->twr_entries;
-    if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, lb); else fill_pass_twiddles<double2>(tw, lb);
-    if ((rc = dalloc(p, &p->tw_pass, std::max<size_t>(tw.size(), 16)))) return fail(rc);
-    if (cudaMemcpy(p->tw_pass, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
-  } else {
-    for (int i = 0; i < p->naxes; ++i) {
-      p->axes[i].tw_off = (int)(tw.size() / sz);
-      if (prec == LSP_C64) fill_twiddles<float2>(tw, p->axes[i].len, p->axes[i].len);
-      else fill_twiddles<double2>(tw, p->axes[i].len, p->axes[i].len);
-    }
-    if (prec == LSP_C64) {
-      // lo parts: exact value minus its FP32 rounding, same layout after the hi parts
-      p->tw_lo = (int)(tw.size() / sz);
-      for (int i = 0; i < p->naxes; ++i) fill_twiddles<float2>(tw, p->axes[i].len, p->axes[i].len, true);
-    }
-    if ((rc = dalloc(p, &p->tw_small, tw.size()))) return fail(rc);
-    if (cudaMemcpy(p->tw_small, tw.data(), tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSP_ERR_CUDA);
-  }
+  // ---- execution path: geometry, twiddle tables, descriptors ----
+  if ((rc = setup_path(p, path))) return fail(rc);
 
   // ---- ||h_chi||^2 per bin ----
   if (aa_mode == LSP_AA_MINL2) {
@@ -499,10 +575,6 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   }
   if (p->max_norm2 < kKLutMax && (rc = dalloc(p, &p->klut, (p->max_norm2 + 1) * sz))) return fail(rc);
 
-  // ---- kernel descriptors ----
-  if (p->path == kPathMultipass) rc = multipass_upload_desc(p, 0);
-  else if (p->path == kPathSmall) rc = small_upload_desc(p, 0);
-  if (rc) return fail(rc);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSP_ERR_CUDA);
   *out = p;
   return LSP_OK;
@@ -552,8 +624,8 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
   int rc = build_phase_tables(p, dt, s);
   if (rc) return rc;
   rc = p->path == kPathMultipass ? multipass_steps(p, nsteps, s)
-       : p->path == kPathRank2   ? r2_steps_on(p, p->u, nsteps, s)
-                                 : small_steps(p, nsteps, s);
+       : p->path == kPathSmall   ? small_steps(p, nsteps, s)
+                                 : s4_steps_on(p, p->u, nsteps, s);
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return LSP_OK;
@@ -577,8 +649,8 @@ int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device,
   int src_prec = p->prec;
   if (space == LSP_SPACE_SPECTRAL) {
     int rc = p->path == kPathMultipass ? multipass_spectral(p, s)
-             : p->path == kPathRank2   ? r2_spectral(p, s)
-                                       : small_spectral(p, s);
+             : p->path == kPathSmall   ? small_spectral(p, s)
+                                       : s4_spectral(p, s);
     if (rc) return rc;
     src = p->stage;
     src_prec = LSP_C128;
@@ -655,11 +727,76 @@ int lsp_index_table(lsp_plan p, int32_t* h) {
   return rc;
 }
 
+int lsp_plan_paths(lsp_plan p, int* mask) {
+  if (!p || !mask) return LSP_ERR_BAD_ARG;
+  *mask = 0;
+  for (int c = 0; c < kNumPaths; ++c)
+    if (path_available(p, c)) *mask |= 1 << c;
+  return LSP_OK;
+}
+
+int lsp_plan_set_path(lsp_plan p, int path) {
+  if (!p || path < 0 || path >= kNumPaths) return LSP_ERR_BAD_ARG;
+  if (!path_available(p, path)) return LSP_ERR_UNSUPPORTED;
+  if (path == p->path) return LSP_OK;
+  DeviceGuard g(p->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return LSP_ERR_CUDA;
+  int rc = setup_path(p, path);
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = LSP_ERR_CUDA;
+  return rc;
+}
+
+int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* chosen, double* ms) {
+  if (!p || nsteps < 1 || !isfinite(dt)) return LSP_ERR_BAD_ARG;
+  if (*p->err_host != 0) return *p->err_host;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->ntot * csize(p->prec);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LSP_ERR_CUDA;
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, bytes) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int orig = p->path;
+  int best = -1, rc = LSP_OK;
+  float best_ms = 0.f;
+  for (int c = 0; c < kNumPaths && !rc; ++c) {
+    if (ms) ms[c] = -1.0;
+    if (!path_available(p, c)) continue;
+    if (c != p->path && (rc = setup_path(p, c))) break;
+    if ((rc = build_phase_tables(p, dt, s))) break;
+    if (cudaMemcpyAsync(scratch, p->u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
+    if ((rc = path_steps_on(p, scratch, 2, s))) break;            // warm-up: every kernel of the path once
+    cudaEventRecord(e0, s);
+    if ((rc = path_steps_on(p, scratch, nsteps, s))) break;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
+    int err = 0;
+    cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) { rc = err; break; }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (ms) ms[c] = t;
+    if (best < 0 || t < best_ms) { best = c; best_ms = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  const int keep = rc ? orig : best;
+  if (keep >= 0 && keep != p->path) {
+    const int rc2 = setup_path(p, keep);
+    if (!rc) rc = rc2;
+  }
+  if (chosen) *chosen = p->path;
+  return rc;
+}
+
 int lsp_plan_info(lsp_plan p, int64_t* info) {
   if (!p || !info) return LSP_ERR_BAD_ARG;
   info[0] = p->ntot;
-  info[1] = p->path != kPathSmall ? p->N1 : p->n[p->r - 1];
-  info[2] = p->path != kPathSmall ? p->N2 : (p->r == 2 ? p->n[0] : 1);
+  info[1] = p->N1;
+  info[2] = p->N2;
   info[3] = p->path;
   info[4] = p->prec;
   info[5] = (int64_t)p->bytes;

@@ -4,8 +4,8 @@
 //  * multipass instances: one group per lattice size 2^m (kernels are
 //    specialised per size); each group is a head sweep, one persistent
 //    cooperative launch over the tiles of all its instances, and a tail sweep;
-//  * rank-2 multipass instances (2^26 points and the like, each enough to
-//    fill the GPU): stepped one after another.
+//  * four-sweep instances (rank-2, and rank-1 beyond the two-sweep sizes;
+//    2^24 points and more, each enough to fill the GPU): stepped one after another.
 // Each instance's phase tables are built with its own dt on every call.
 #include <string.h>
 
@@ -57,6 +57,7 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   lsp_batch b = new (std::nothrow) lsp_batch_s();
   if (!b) return LSP_ERR_OOM;
   b->plans.assign(plans, plans + count);
+  for (int i = 0; i < count; ++i) b->paths.push_back(plans[i]->path);
   b->prec = prec;
   b->device = dev;
   DeviceGuard g(dev);
@@ -65,7 +66,7 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   std::map<int, std::vector<int>> by_m;
   for (int i = 0; i < count; ++i) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
-    else if (plans[i]->path == kPathRank2) b->rank2_ids.push_back(i);
+    else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4) b->seq_ids.push_back(i);
     else b->small_ids.push_back(i);
   }
   // SMEM-resident group
@@ -118,7 +119,7 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
 int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream) {
   if (!b || !dt || nsteps < 0) return LSP_ERR_BAD_ARG;
   for (size_t i = 0; i < b->plans.size(); ++i)
-    if (!isfinite(dt[i])) return LSP_ERR_BAD_ARG;
+    if (!isfinite(dt[i]) || b->plans[i]->path != b->paths[i]) return LSP_ERR_BAD_ARG;
   if (*b->err_host != 0) return *b->err_host;
   if (nsteps == 0) return LSP_OK;
   DeviceGuard g(b->device);
@@ -131,8 +132,8 @@ int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream)
     int rc = small_batch_launch(b->prec, b->small_desc, (int)b->small_ids.size(), b->small_max_n, nsteps, s);
     if (rc) return rc;
   }
-  for (int i : b->rank2_ids) {   // each fills the GPU by itself
-    int rc = r2_steps_on(b->plans[i], b->plans[i]->u, nsteps, s);
+  for (int i : b->seq_ids) {     // each fills the GPU by itself
+    int rc = s4_steps_on(b->plans[i], b->plans[i]->u, nsteps, s);
     if (rc) return rc;
   }
   for (auto& c : b->classes) {

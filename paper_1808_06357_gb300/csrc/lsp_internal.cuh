@@ -32,7 +32,9 @@ constexpr long long kKLutMax = 1ll << 20;
 // Bounded device-side waits (grid barrier): spins of ~100 ns each.
 constexpr long long kSpinLimit = 1ll << 25;
 
-enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2 };
+// Execution paths (lsp_plan_info [3]): rank-1 two-sweep multipass, SMEM-resident,
+// rank-2 four-sweep, rank-1 four-sweep.
+enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2, kPathRank1x4 = 3, kNumPaths = 4 };
 
 // --------------------------------------------------------------------------
 // Plan
@@ -58,8 +60,9 @@ struct lsp_plan_s {
   int aa_mode = LSP_AA_MINL2;
   int path = lsp::kPathSmall;
 
-  // multipass geometry (rank-1, n = N1 * N2, row length N1 contiguous;
-  // rank-2 multipass: logN1 = log2 n_1, logN2 = log2 n_2)
+  // multipass geometry: rank-1 n = N1 * N2 with rows of N1 contiguous points
+  // (two-sweep and four-sweep paths); rank-2 four-sweep: logN1 = log2 n_1,
+  // logN2 = log2 n_2 (rows of n_2 points), N1 = n_2, N2 = n_1
   int logn = 0, N1 = 1, N2 = 1, logN1 = 0, logN2 = 0, logLmax = 0;
 
   // SMEM-resident geometry
@@ -75,11 +78,12 @@ struct lsp_plan_s {
   void* Pf = nullptr;         // exp(-i dt v / gamma), kappa order, encoded
   void* K = nullptr;          // exp(-i gamma 2 pi^2 |h|^2 dt) in the kernel's bin order
   void* klut = nullptr;       // K per value of ||h||^2 = 0..max_norm2 (when max_norm2 < kKLutMax)
-  void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (multipass); W_n1^k, k < n1 (rank-2 multipass)
-  void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (multipass)
+  void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (two-sweep); W_{2^M1}^k (four-sweep: n1 or N2 points)
+  void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (two-sweep); W_n^k, k < N2 (rank-1 four-sweep)
+  void* tw_coarse = nullptr;  // W_N1^k, k < N1 (rank-1 four-sweep)
   void* tw_pass = nullptr;    // per-pass line twiddles: row lines, then column lines
   int twr_entries = 0;        // entries of the row-line part of tw_pass
-  int twa_entries = 0;        // rank-2: entries of the second part (the third follows)
+  int twa_entries = 0;        // four-sweep: entries of the second part (the third follows)
   void* tw_small = nullptr;   // per-axis W_len^k tables (SMEM-resident path)
   void* stage = nullptr;      // n complex128 staging buffer (conversions, spectral output)
   void* work = nullptr;       // n complex (plan precision): scratch copy for spectral output
@@ -98,7 +102,8 @@ struct lsp_plan_s {
 struct lsp_batch_s {
   std::vector<lsp_plan> plans;   // borrowed
   int prec = LSP_C64;
-  std::vector<int> rank2_ids;    // rank-2 multipass instances, stepped one after another
+  std::vector<int> seq_ids;      // four-sweep instances, stepped one after another
+  std::vector<int> paths;        // each plan's execution path when the batch was made
   int device = 0;
   // SMEM-resident instances: one CTA each, one launch for all of them
   std::vector<int> small_ids;
@@ -258,10 +263,13 @@ void multipass_fill_desc(lsp_plan p, void* host_out, int* ncol, int* nrow);
 int multipass_batch_steps(int prec, int m, const void* ddesc, const int2* colmap, const int2* rowmap, int ninst,
                           int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s);
 
-// rank-2 multipass (n_1 = 2^m1, n_2 = 2^m2)
-bool r2_supports(int prec, int m1, int m2);
-int r2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
-int r2_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
+// four-sweep paths: rank-2 (n_1 = 2^m1, n_2 = 2^m2) and rank-1 (n = 2^m)
+bool s4_supports_rank2(int prec, int m1, int m2);
+bool s4_supports_rank1(int prec, int m);
+int s4_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
+int s4_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
+// steps of the plan's current path on a state buffer of the plan's geometry
+int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; }
 

@@ -107,9 +107,6 @@ template <typename T, int M> struct SmemLayout {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T ldst(const T* p) { return __ldcg(p); }
-template <typename T> __device__ __forceinline__ void stst(T* p, T v) { __stcg(p, v); }
-template <typename T> __device__ __forceinline__ T ldtab(const T* p) { return __ldcs(p); }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));

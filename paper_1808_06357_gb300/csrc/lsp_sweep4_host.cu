@@ -1,0 +1,131 @@
+// Host side of the four-sweep Strang step (rank-2 lattices, and rank-1
+// lattices on the four-sweep schedule): descriptors, launches, step driver,
+// spectral output.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "lsp_sweep4.cuh"
+
+namespace lsp {
+
+// Template shape of a plan: rank-2 (M1, M2) = (log2 n1, log2 n2); rank-1
+// (M1, M2) = (log2 N2, log2 N1), rows of N1 points.
+static bool s4_lookup(lsp_plan p, S4Kernels* k) {
+  if (p->path == kPathRank2) return s4_kernels_rank2(p->prec, p->logN1, p->logN2, k);
+  if (p->path == kPathRank1x4) return s4_kernels_rank1(p->prec, p->logn, k);
+  return false;
+}
+
+bool s4_supports_rank2(int prec, int m1, int m2) {
+  S4Kernels k;
+  return s4_kernels_rank2(prec, m1, m2, &k);
+}
+
+bool s4_supports_rank1(int prec, int m) {
+  S4Kernels k;
+  return s4_kernels_rank1(prec, m, &k);
+}
+
+template <typename T> static S4Inst<T> s4_inst(lsp_plan p, void* state) {
+  S4Inst<T> I{};
+  I.u = (T*)state;
+  I.Ph = (const T*)p->Ph;
+  I.Pf = (const T*)p->Pf;
+  I.K = (const T*)p->K;
+  const T* tw = (const T*)p->tw_pass;
+  I.tw_rows = tw;
+  I.tw_a = tw + p->twr_entries;
+  I.tw_b = tw + p->twr_entries + p->twa_entries;
+  I.tw_col = (const T*)p->tw_line;
+  I.tw_bl = (const T*)p->tw_coarse;
+  I.tw_bf = (const T*)p->tw_fine;
+  I.spec = (double2*)p->stage;
+  I.err = p->err;
+  I.inv_n = (decltype(I.inv_n))(1.0 / (double)p->ntot);
+  return I;
+}
+
+// Grid of one sweep kernel: as many CTAs as fit on the device at once (at most
+// one per tile), computed once per (device, kernel).
+static int s4_grid(const void* fn, int nt, size_t smem, int* grid) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> cache;
+  int dev = 0;
+  LSP_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, fn});
+  if (it != cache.end()) { *grid = it->second; return LSP_OK; }
+  int per_sm = 0, sms = 0;
+  LSP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
+  LSP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) return LSP_ERR_UNSUPPORTED;
+  *grid = per_sm * sms;
+  cache[{dev, fn}] = *grid;
+  return LSP_OK;
+}
+
+template <typename T> static int s4_launch(const void* fn, const S4Inst<T>& I, int ntiles, cudaStream_t s) {
+  constexpr int NT = S4Cfg<T>::NT;
+  constexpr size_t smem = (size_t)S4Cfg<T>::TILE * sizeof(T);   // exchange buffer
+  int grid = 0;
+  int rc = s4_grid(fn, NT, smem, &grid);
+  if (rc) return rc;
+  grid = std::max(1, std::min(ntiles, grid));
+  void* args[] = {(void*)&I};
+  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s));
+  return LSP_OK;
+}
+
+// N steps: P-sweep head, then per step the three other sweeps and the next
+// P-sweep (mid), and the P-sweep tail.  Sweep geometries: rows (0), A / X (1), B / Y (2).
+template <typename T> static int s4_steps_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  S4Kernels K;
+  if (!s4_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
+  const S4Inst<T> I = s4_inst<T>(p, state);
+  const bool r2 = p->path == kPathRank2;
+  // kernel, geometry of each sweep of a step in order
+  const int head = r2 ? kR2Head : kXHead, mid = r2 ? kR2Mid : kXMid, tail = r2 ? kR2Tail : kXTail;
+  const int pg = r2 ? 0 : 1;                                       // geometry of the P sweep
+  const int seq[3] = {r2 ? kR2A : kY, r2 ? kR2B : kZ, r2 ? kR2AInv : kYInv};
+  const int geo[3] = {r2 ? 1 : 2, r2 ? 2 : 0, r2 ? 1 : 2};
+  int rc = LSP_OK;
+  for (int64_t st = 0; st < nsteps && !rc; ++st) {
+    rc = s4_launch<T>(K.k[st == 0 ? head : mid], I, K.ntiles[pg], s);
+    for (int i = 0; i < 3 && !rc; ++i) rc = s4_launch<T>(K.k[seq[i]], I, K.ntiles[geo[i]], s);
+  }
+  if (!rc) rc = s4_launch<T>(K.k[tail], I, K.ntiles[pg], s);
+  return rc;
+}
+
+// Spectral coefficients of the current state into p->stage (chi order, c128),
+// on a scratch copy of the state.
+template <typename T> static int s4_spectral_impl(lsp_plan p, cudaStream_t s) {
+  S4Kernels K;
+  if (!s4_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
+  LSP_CUDA_TRY(cudaMemcpyAsync(p->work, p->u, (size_t)p->ntot * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  const S4Inst<T> I = s4_inst<T>(p, p->work);
+  int rc;
+  if (p->path == kPathRank2) {
+    rc = s4_launch<T>(K.k[kR2RowFwd], I, K.ntiles[0], s);
+    if (!rc) rc = s4_launch<T>(K.k[kR2A], I, K.ntiles[1], s);
+    if (!rc) rc = s4_launch<T>(K.k[kR2BFwd], I, K.ntiles[2], s);
+  } else {
+    rc = s4_launch<T>(K.k[kXFwd], I, K.ntiles[1], s);
+    if (!rc) rc = s4_launch<T>(K.k[kY], I, K.ntiles[2], s);
+    if (!rc) rc = s4_launch<T>(K.k[kZFwd], I, K.ntiles[0], s);
+  }
+  return rc;
+}
+
+int s4_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  return p->prec == LSP_C64 ? s4_steps_impl<float2>(p, state, nsteps, s) : s4_steps_impl<double2>(p, state, nsteps, s);
+}
+
+int s4_spectral(lsp_plan p, cudaStream_t s) {
+  return p->prec == LSP_C64 ? s4_spectral_impl<float2>(p, s) : s4_spectral_impl<double2>(p, s);
+}
+
+}  // namespace lsp

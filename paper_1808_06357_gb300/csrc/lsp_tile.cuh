@@ -137,6 +137,12 @@ template <> struct Swz<double2> {  // 8 x 16 B per 128 B bank row
   static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 3) & 7); }
 };
 
+// State loads and stores bypass L1 (each point is touched once per sweep);
+// phase tables are read once per step (streaming).
+template <typename T> __device__ __forceinline__ T ldst(const T* p) { return __ldcg(p); }
+template <typename T> __device__ __forceinline__ void stst(T* p, T v) { __stcg(p, v); }
+template <typename T> __device__ __forceinline__ T ldtab(const T* p) { return __ldcs(p); }
+
 // ---------------------------------------------------------------------------
 // Compile-time line geometry
 // ---------------------------------------------------------------------------

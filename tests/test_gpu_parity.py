@@ -153,10 +153,22 @@ def test_multipass_1000_steps(lib, prec):
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_c2_full_size_short_run(lib, prec):
-    """C2 at n = 2^22 (4096 x 1024 four-step split), 20 steps against the oracle."""
+    """C2 at n = 2^22, 20 steps against the oracle, on both rank-1 paths: the two-sweep kernel
+    (4096 x 1024 four-step split) and the four-sweep kernels (4096 x 32 x 32)."""
+    import torch
     inst = w.c2(22)
-    got, ref, u0, _ = run_both(lib, inst, prec, 20)
-    assert rel_l2(got, ref) < TOL[prec]
+    P = L.lattice_points(inst.Z, inst.n)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    v, u0 = inst.v(P), inst.u0(P)
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 20)
+    for path in (lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP):
+        plan = make_plan(lib, inst, prec)
+        plan.set_path(path)
+        plan.set_potential(torch.from_numpy(v).cuda())
+        plan.set_state(torch.from_numpy(u0).cuda())
+        plan.strang_steps(inst.dt, 20)
+        assert plan.status() == 0
+        assert rel_l2(host_state(plan), ref) < TOL[prec]
 
 
 def test_free_evolution_closed_form(lib):
@@ -237,5 +249,6 @@ def test_error_codes(lib):
     with pytest.raises(lib.LspError) as e:
         plan.strang_steps(1e-3, -1)
     assert e.value.code == -1
-    with pytest.raises(lib.LspError):
-        lib.Plan(np.array([1, 3]), (1 << 24,), 0.1, prec="c128")   # beyond the multipass limits
+    with pytest.raises(lib.LspError) as e:
+        lib.Plan(np.array([1, 3]), (1 << 26,), 0.1, prec="c128")   # beyond every rank-1 path
+    assert e.value.code == -4
