@@ -151,6 +151,17 @@ int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device,
  */
 int lsp_plan_status(lsp_plan p, void* stream);
 
+/*
+ * lsp_observables -- the conserved quantities of Sec. 3.3 for the current state:
+ *   out[0] = ||u_a||^2 = (1/n) sum_kappa |u_kappa|^2,
+ *   out[1] = <H u_a, u_a> = sum_chi (gamma/2) 4 pi^2 ||h_chi||^2 |uhat_chi|^2
+ *            + (1/gamma) (1/n) sum_kappa v_kappa |u_kappa|^2,
+ * with H = -(gamma/2) Lap + v / gamma and uhat as for LSP_SPACE_SPECTRAL.  FP64
+ * accumulation in a fixed order (the result does not depend on scheduling).
+ * out: 2 doubles (host).  Synchronises `stream`.  Errors: BAD_ARG, OOM, CUDA, TIMEOUT.
+ */
+int lsp_observables(lsp_plan p, double* out, void* stream);
+
 /* Lattice points p_kappa as n*d doubles (host), row-major (Def. 1). Errors: BAD_ARG, CUDA. */
 int lsp_lattice_points(lsp_plan p, double* x);
 

@@ -51,6 +51,7 @@ def _declare(lib):
         "lsp_index_table": (I, [P, P]),
         "lsp_plan_info": (I, [P, P]),
         "lsp_plan_paths": (I, [P, C.POINTER(C.c_int)]),
+        "lsp_observables": (I, [P, P, P]),
         "lsp_plan_set_path": (I, [P, I]),
         "lsp_plan_autotune": (I, [P, D, I64, P, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "lsp_batch_create": (I, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), I]),
@@ -216,6 +217,13 @@ class Plan:
         _check(self._lib.lsp_get_state(self._h, ptr, pc, sp, dev, _stream_ptr(stream)), "lsp_get_state")
         return out
 
+    def observables(self, stream=None):
+        """(norm^2, energy) of the current state (lsp_observables, Sec. 3.3)."""
+        out = np.zeros(2, dtype=np.float64)
+        _check(self._lib.lsp_observables(self._h, C.c_void_p(out.ctypes.data), _stream_ptr(stream)),
+               "lsp_observables")
+        return float(out[0]), float(out[1])
+
     def status(self, stream=None) -> int:
         return int(self._lib.lsp_plan_status(self._h, _stream_ptr(stream)))
 
@@ -274,6 +282,13 @@ class Batch:
         dt = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
         _check(self._lib.lsp_batch_steps(self._h, C.c_void_p(dt.ctypes.data), int(nsteps), _stream_ptr(stream)),
                "lsp_batch_steps")
+
+    def observables(self, stream=None):
+        """(norm^2, energy) of the current state (lsp_observables, Sec. 3.3)."""
+        out = np.zeros(2, dtype=np.float64)
+        _check(self._lib.lsp_observables(self._h, C.c_void_p(out.ctypes.data), _stream_ptr(stream)),
+               "lsp_observables")
+        return float(out[0]), float(out[1])
 
     def status(self, stream=None) -> int:
         return int(self._lib.lsp_batch_status(self._h, _stream_ptr(stream)))

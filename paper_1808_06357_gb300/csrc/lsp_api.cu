@@ -204,6 +204,43 @@ static int launch_convert(const void* src, int sp, void* dst, int dp, long long 
 
 static size_t csize(int prec) { return prec == LSP_C64 ? sizeof(float2) : sizeof(double2); }
 
+// Observables (Sec. 3.3): per-block FP64 partial sums of |u_k|^2, v_k |u_k|^2 and
+// ||h_chi||^2 |uhat_chi|^2 (spectral coefficients in chi order), summed on the host in
+// block order, so that the result does not depend on scheduling.
+constexpr int kObsBlocks = 1024, kObsThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kObsThreads) obs_partials(const T* __restrict__ u, const double* __restrict__ v,
+                                                           const double2* __restrict__ uhat,
+                                                           const int32_t* __restrict__ norm2, long long n,
+                                                           double* __restrict__ part) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (long long i = blockIdx.x * (long long)kObsThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kObsThreads) {
+    const double ur = (double)u[i].x, ui = (double)u[i].y;
+    const double m = ur * ur + ui * ui;
+    a += m;
+    b += v[i] * m;
+    const double2 w = uhat[i];
+    c += (double)norm2[i] * (w.x * w.x + w.y * w.y);
+  }
+  __shared__ double sa[kObsThreads], sb[kObsThreads], sc[kObsThreads];
+  sa[threadIdx.x] = a; sb[threadIdx.x] = b; sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = kObsThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sb[threadIdx.x] += sb[threadIdx.x + w];
+      sc[threadIdx.x] += sc[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = sa[0];
+    part[3 * blockIdx.x + 1] = sb[0];
+    part[3 * blockIdx.x + 2] = sc[0];
+  }
+}
+
 // Phase tables of one plan for step size dt (a0), FP64 arguments in turns:
 //   P_half: -dt v / (4 pi gamma),  K: -pi gamma dt ||h||^2.
 int build_phase_tables(lsp_plan p, double dt, cudaStream_t s) {
@@ -250,9 +287,24 @@ static void factorize(int len, SmallAxis& ax) {
   if (rem > 1 && ax.nfac < 24) ax.fac[ax.nfac++] = rem;
 }
 
+// One table entry exp(-2 pi i f) (f in turns, reduced to [-1/2, 1/2]) in the
+// multipass tables' form: complex128 (cos, sin); complex64 (cos - 1, sin) with
+// cos - 1 = -2 sin^2(pi f) evaluated without cancellation (see twmul).
+template <typename T> static T table_entry(double f) {
+  using R = decltype(T{}.x);
+  const double ang = -2.0 * M_PI * f;
+  if (LSP_TW_WM1 && sizeof(R) == sizeof(float)) {
+    const double sh = sin(M_PI * f);
+    return T{(R)(-2.0 * sh * sh), (R)sin(ang)};
+  }
+  return T{(R)cos(ang), (R)sin(ang)};
+}
+
 template <typename T>
-static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long long denom, bool lo = false) {
-  // entries exp(-2 pi i k / denom), k < len (lo: the rounding residue of each entry)
+static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long long denom, bool lo = false,
+                          bool table_form = false) {
+  // entries exp(-2 pi i k / denom), k < len (lo: the rounding residue of each entry;
+  // table_form: the multipass tables' form of table_entry)
   using R = decltype(T{}.x);
   size_t off = buf.size();
   buf.resize(off + (size_t)len * sizeof(T));
@@ -262,6 +314,7 @@ static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long l
     long long kk = k % denom;
     double f = (double)kk / (double)denom;
     if (f > 0.5) f -= 1.0;
+    if (table_form) { t[k] = table_entry<T>(f); continue; }
     double ang = -2.0 * M_PI * f;
     double c = cos(ang), s = sin(ang);
     R ch = (R)c, sh = (R)s;
@@ -273,7 +326,6 @@ static void fill_twiddles(std::vector<unsigned char>& buf, long long len, long l
 // Per-pass twiddle tables of a line of length 2^logL (radix plan R1, 16, ..., 16):
 // pass S >= 2 with span Ns stores W_{16 Ns}^{jm r} at [r-1][jm], r = 1..15, jm < Ns.
 template <typename T> static void fill_pass_twiddles(std::vector<unsigned char>& buf, int logL) {
-  using R = decltype(T{}.x);
   const int logR1 = logL % 4 == 0 ? 4 : logL % 4;
   const int P = (logL - logR1) / 4 + 1;
   for (int S = 2; S <= P; ++S) {
@@ -282,9 +334,7 @@ template <typename T> static void fill_pass_twiddles(std::vector<unsigned char>&
       for (long long jm = 0; jm < Ns; ++jm) {
         double f = (double)((jm * r) % den) / (double)den;
         if (f > 0.5) f -= 1.0;
-        T e;
-        e.x = (R)cos(-2.0 * M_PI * f);
-        e.y = (R)sin(-2.0 * M_PI * f);
+        const T e = table_entry<T>(f);
         size_t off = buf.size();
         buf.resize(off + sizeof(T));
         memcpy(buf.data() + off, &e, sizeof(T));
@@ -355,7 +405,10 @@ static int setup_path(lsp_plan p, int path) {
   p->logn = logn > 0 ? logn : 0;
   int rc = LSP_OK;
   auto twid = [&](std::vector<unsigned char>& tw, long long len, long long denom, bool lo = false) {
-    if (prec == LSP_C64) fill_twiddles<float2>(tw, len, denom, lo); else fill_twiddles<double2>(tw, len, denom, lo);
+    // SMEM path: plain entries with hi/lo parts; multipass paths: the tables' form (table_entry)
+    const bool form = path != kPathSmall;
+    if (prec == LSP_C64) fill_twiddles<float2>(tw, len, denom, lo, form);
+    else fill_twiddles<double2>(tw, len, denom, lo, form);
   };
   auto passes = [&](std::vector<unsigned char>& tw, int logL) {
     if (prec == LSP_C64) fill_pass_twiddles<float2>(tw, logL); else fill_pass_twiddles<double2>(tw, logL);
@@ -629,6 +682,38 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return LSP_OK;
+}
+
+int lsp_observables(lsp_plan p, double* out, void* stream) {
+  if (!p || !out) return LSP_ERR_BAD_ARG;
+  if (*p->err_host != 0) return *p->err_host;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = p->path == kPathMultipass ? multipass_spectral(p, s)
+           : p->path == kPathSmall   ? small_spectral(p, s)
+                                     : s4_spectral(p, s);
+  if (rc) return rc;
+  double* part = nullptr;
+  if (cudaMallocAsync((void**)&part, 3 * kObsBlocks * sizeof(double), s) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
+  const int blocks = (int)std::min<long long>(kObsBlocks, (p->ntot + kObsThreads - 1) / kObsThreads);
+  if (p->prec == LSP_C64)
+    obs_partials<float2><<<blocks, kObsThreads, 0, s>>>((const float2*)p->u, p->v, (const double2*)p->stage,
+                                                        p->norm2, p->ntot, part);
+  else
+    obs_partials<double2><<<blocks, kObsThreads, 0, s>>>((const double2*)p->u, p->v, (const double2*)p->stage,
+                                                         p->norm2, p->ntot, part);
+  std::vector<double> h(3 * (size_t)blocks);
+  rc = cuda_status(cudaGetLastError());
+  if (!rc) rc = cuda_status(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  cudaFreeAsync(part, s);
+  if (!rc) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc) return rc;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = 0; k < blocks; ++k) { a += h[3 * k]; b += h[3 * k + 1]; c += h[3 * k + 2]; }
+  const double n = (double)p->ntot;
+  out[0] = a / n;                                                        // (1/n) sum |u|^2
+  out[1] = 0.5 * p->gamma * 4.0 * M_PI * M_PI * c + b / (p->gamma * n);  // <H u, u>
+  return *p->err_host;
 }
 
 int lsp_plan_status(lsp_plan p, void* stream) {

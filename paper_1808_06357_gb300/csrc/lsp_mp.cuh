@@ -142,7 +142,7 @@ template <typename T, int M>
 __device__ __forceinline__ T big_tw(const T* twl, const T* twf, unsigned k1, unsigned xi2) {
   const unsigned a = (k1 * xi2) & ((1u << M) - 1u);
   constexpr int sh = M - Split<M>::LN1;
-  return cmul(twl[a >> sh], twf[a & ((1u << sh) - 1u)]);
+  return twprod(twl[a >> sh], twf[a & ((1u << sh) - 1u)]);
 }
 
 // Twiddle tables a pass uses (shared or global).
@@ -183,7 +183,7 @@ __device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T*
     for (int t = 0; t < 16; ++t) {
       const unsigned xi2 = j + (t << (LOGL - 4));
       T x = FROM == kFromPre ? pre[(xi2 << G::LOGC) + b] : ldst(u + (k1 + (xi2 << lN1)));
-      v[t] = cmulc(x, big_tw<T, M>(tw.l, tw.f, k1, xi2));
+      v[t] = twmulc(x, big_tw<T, M>(tw.l, tw.f, k1, xi2));
     }
   } else {
 #pragma unroll
@@ -225,7 +225,7 @@ __device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T*
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
       const unsigned xi2 = j + (t << (LOGL - 4));
-      stst(u + (k1 + (xi2 << lN1)), cmul(v[t], big_tw<T, M>(tw.l, tw.f, k1, xi2)));
+      stst(u + (k1 + (xi2 << lN1)), twmul(v[t], big_tw<T, M>(tw.l, tw.f, k1, xi2)));
     }
   } else {
 #pragma unroll

@@ -202,7 +202,7 @@ struct Line {
         int b, j; bm<LR>(q, b, j);
         const T* tq = tw + tw_off(S) + (j & ((1 << LNS) - 1));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tq[(r - 1) << LNS]);
+        for (int r = 1; r < R; ++r) v[q * R + r] = twmul(v[q * R + r], tq[(r - 1) << LNS]);
       }
       bfly<R, -1>(&v[q * R]);
     }
@@ -255,7 +255,7 @@ struct Line {
         int b, j; bm<LR>(q, b, j);
         const T* tq = tw + tw_off(S) + (j & ((1 << LNS) - 1));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[q * R + r] = cmulc(v[q * R + r], tq[(r - 1) << LNS]);
+        for (int r = 1; r < R; ++r) v[q * R + r] = twmulc(v[q * R + r], tq[(r - 1) << LNS]);
       }
     }
   }

@@ -151,3 +151,25 @@ def test_four_sweep_batch_and_adjoint(lib):
     assert p.status() == 0
     assert rel_l2(gv.cpu().numpy(), gv_ref) < 1e-9
     assert rel_l2(gu.cpu().numpy(), gu_ref) < 1e-9
+
+
+def test_c2_1000_steps_complex64_against_complex128(lib):
+    """The bench workload (d = 6, n = 2^22, 1000 steps): the complex64 four-sweep path against
+    the complex128 two-sweep path (itself pinned to the oracle), and the complex64 norm drift."""
+    import torch
+    inst = w.c2(22)
+    pts = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64").lattice_points()
+    v, u0 = torch.from_numpy(inst.v(pts)).cuda(), torch.from_numpy(inst.u0(pts)).cuda()
+    out = {}
+    for prec, path in (("c64", lib.PATH_RANK1_4SWEEP), ("c128", lib.PATH_MULTIPASS)):
+        plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec)
+        plan.set_path(path)
+        plan.set_potential(v)
+        plan.set_state(u0)
+        n0, _ = plan.observables()
+        plan.strang_steps(inst.dt, 1000)
+        n1, _ = plan.observables()
+        out[prec] = (plan.get_state(prec="c128"), abs(n1 / n0 - 1))
+    err = float(torch.linalg.norm(out["c64"][0] - out["c128"][0]) / torch.linalg.norm(out["c128"][0]))
+    print(f"C2 1000 steps: complex64 four-sweep rel-L2 {err:.3e}, norm drift {out['c64'][1]:.3e}")
+    assert err < 5e-5 and out["c64"][1] < 5e-5 and out["c128"][1] < 1e-12

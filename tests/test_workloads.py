@@ -46,3 +46,34 @@ def test_plane_waves_equal_exponentials_at_points():
     got = w.plane_waves(xi, c, inst.n)
     ref = np.exp(2j * np.pi * (P @ H.T.astype(np.float64))) @ c
     assert np.allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_table1_vectors_match_the_golden_fixture():
+    """The workload module's Table 1 vectors are the cited fixture's, row by row."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_generating_vectors.txt")
+    rows = [list(map(int, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    for r in rows:
+        d, m, z = r[0], r[1], r[2:]
+        if d <= 3:
+            assert list(w.table1_z(d, m)) == z
+        else:
+            assert list(w.TABLE1_Z12) == z
+            for dd in range(4, 13):
+                assert list(w.table1_z(dd, 25)) == z[:dd]
+
+
+def test_paper_initial_conditions():
+    """g1 peaks at the packet centre (x_1 = 3/4, x_j = 1/2) and is separable; g2's factors are
+    hats of half-width sqrt(gamma)/4 in x; both have unit lattice-rule norm."""
+    inst = w.paper_instance(2, 18, init="g1", gamma=0.5)
+    P = L.lattice_points(inst.Z, inst.n)
+    g = inst.u0(P)
+    assert abs(np.mean(np.abs(g) ** 2) - 1) < 1e-12
+    k = int(np.argmax(np.abs(g)))
+    assert np.allclose(P[k], [0.75, 0.5], atol=5e-3)
+    gamma = 0.01
+    h = w.paper_g2(P, gamma)
+    assert abs(np.mean(np.abs(h) ** 2) - 1) < 1e-12 and np.all(h.real >= 0)
+    far = np.abs(P[:, 1] - 0.5) > np.sqrt(gamma) / 4 + 1e-12
+    assert np.all(h[far] == 0)

@@ -327,6 +327,61 @@ def c5_fields(inst: "Instance", rows_per_chunk: int = 256):
     return v, u
 
 
+# --------------------------------------------------------------------------
+# The paper's own experiments (Sec. 3.1 Table 1; Sec. 3.2 g1, g2, v1, v2)
+# --------------------------------------------------------------------------
+# Generating vectors of Table 1 (Sec. 3.1): d = 2 and 3 have their own rows; for
+# d = 4..12 the paper uses n = 2^25 and the first d components of the 12-vector.
+TABLE1_ROWS = {(2, 18): (1, 100135), (2, 20): (1, 443165), (3, 22): (1, 1737355, 261247),
+               (3, 25): (1, 12386359, 15699201)}
+TABLE1_Z12 = (1, 12386359, 15699201, 6807287, 13966305, 6107923, 4432603, 2304135, 7323801, 5705679,
+              5643703, 3867405)
+
+
+def table1_z(d: int, n_log2: int) -> np.ndarray:
+    if (d, n_log2) in TABLE1_ROWS:
+        return np.array(TABLE1_ROWS[(d, n_log2)], dtype=np.int64)
+    if 4 <= d <= 12 and n_log2 == 25:
+        return np.array(TABLE1_Z12[:d], dtype=np.int64)
+    raise ValueError(f"Table 1 has no lattice for d={d}, n=2^{n_log2}")
+
+
+def _paper_offsets(points: np.ndarray) -> np.ndarray:
+    """2 pi x_j - c_j with c_1 = 3 pi / 2 and c_j = pi for j >= 2 (the packet centre of g1, g2)."""
+    pts = np.asarray(points, dtype=np.float64)
+    c = np.full(pts.shape[1], np.pi)
+    c[0] = 1.5 * np.pi
+    return 2.0 * np.pi * pts - c
+
+
+def _unit(u: np.ndarray) -> np.ndarray:
+    return u / math.sqrt(float(np.mean(np.abs(u) ** 2)))
+
+
+def paper_g1(points: np.ndarray, gamma: float) -> np.ndarray:
+    """Sec. 3.2 "Gaussian" g1: exp(-sum_j (2 pi x_j - c_j)^2 / gamma), unit lattice-rule norm."""
+    y = _paper_offsets(points)
+    return _unit(np.exp(-np.sum(y * y, axis=1) / gamma).astype(np.complex128))
+
+
+def paper_g2(points: np.ndarray, gamma: float) -> np.ndarray:
+    """Sec. 3.2 "Hat" g2: prod_j (1 - 2 |2 pi x_j - c_j| / (pi sqrt(gamma))), each factor taken
+    as its positive part, unit lattice-rule norm."""
+    y = np.abs(_paper_offsets(points))
+    f = np.clip(1.0 - 2.0 * y / (np.pi * math.sqrt(gamma)), 0.0, None)
+    return _unit(np.prod(f, axis=1).astype(np.complex128))
+
+
+def paper_instance(d: int, n_log2: int, init: str = "g1", pot: str = "v2", gamma: float = 0.5,
+                   dt: float = 1e-3, nsteps: int = 1000) -> Instance:
+    """A Sec. 3.2 experiment on a Table 1 lattice: initial condition g1 or g2, potential v1 or v2."""
+    z = table1_z(d, n_log2)
+    g = paper_g1 if init == "g1" else paper_g2
+    return Instance(name=f"paper d={d} n=2^{n_log2} {init} {pot} gamma={gamma}", d=d, n=(1 << n_log2,), Z=z,
+                    gamma=gamma, dt=dt, nsteps=nsteps, v=v_smooth if pot == "v1" else v_harmonic,
+                    u0=lambda p, _g=g, _gm=gamma: _g(p, _gm))
+
+
 @dataclass
 class Instance:
     """One TDSE problem: lattice, physics parameters and input functions."""
