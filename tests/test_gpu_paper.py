@@ -135,3 +135,26 @@ def test_table1_high_dimension_full_size(lib):
         del plan
     r = float(torch.linalg.norm(outs["c64"] - outs["c128"]) / torch.linalg.norm(outs["c128"]))
     assert r < 5e-5
+
+
+def test_initial_error_matches_oracle_coefficients(lib):
+    """Sec. 3.4 e_total of g1 (gamma = 1) on the d = 2 Table 1 lattices: the library's lattice-rule
+    coefficients give the same e_total as the oracle's, and it falls from n = 2^18 to 2^20."""
+    import math
+    from paper_1808_06357_gb300 import experiments as X
+    r18 = X.initial_error(d=2, n_log2=18, gamma=1.0)
+    r20 = X.initial_error(d=2, n_log2=20, gamma=1.0)
+    z = w.table1_z(2, 18)
+    n = (1 << 18,)
+    P = L.lattice_points(z, n)
+    cs = np.array(X.g1_centres(2))
+    norm2 = X.g1_norm_factor(cs[0], 1.0) * X.g1_norm_factor(cs[1], 1.0)
+    u = np.exp(-np.sum((2 * np.pi * P - cs) ** 2, axis=1)) / math.sqrt(norm2)
+    ga = S.coeffs(u, n)
+    _, B = L.minl2_norms_dp(z, n)
+    H = lib.Plan(z, n, 1.0, prec="c128").index_table()
+    assert np.array_equal(L.chi_index(H, z, n), np.arange(n[0]))
+    g = X.g1_coefficients(H, 1.0)
+    e = math.sqrt(max(0.0, 1 - np.sum(np.abs(g) ** 2)) + np.sum(np.abs(g - ga) ** 2))
+    assert abs(r18["e_total"] - e) < 1e-9 * e
+    assert r20["e_total"] < r18["e_total"]
