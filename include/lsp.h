@@ -134,6 +134,19 @@ int lsp_set_state(lsp_plan p, const void* u, int u_prec, int on_device, void* st
 int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream);
 
 /*
+ * lsp_strang_composed -- nsteps steps of a composition of Strang steps,
+ *     u <- S(w[s-1] dt) ... S(w[1] dt) S(w[0] dt) u,   S as in lsp_strang_steps,
+ * for higher-order splitting (not in the paper, which names higher-order
+ * splitting as future work, Sec. 5).  The symmetric triple w = (c, 1 - 2c, c),
+ * c = 1 / (2 - 2^(1/3)), gives fourth order.  Each stage is a full Strang step
+ * of its own size; one set of phase tables per distinct weight is built per
+ * call (3 n complex of device memory for each weight after the first).
+ *   nstages  1..16 stage weights in w (host).
+ * Errors: BAD_ARG, OOM, CUDA, TIMEOUT (as lsp_strang_steps).
+ */
+int lsp_strang_composed(lsp_plan p, double dt, int64_t nsteps, int nstages, const double* w, void* stream);
+
+/*
  * lsp_get_state -- copy the state out.
  *   out_prec  LSP_C64 or LSP_C128 element type of `out`.
  *   space     LSP_SPACE_PHYSICAL: samples u(p_kappa), kappa order;

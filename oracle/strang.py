@@ -138,6 +138,18 @@ def plane_wave_evolution(xi: np.ndarray, norms2: np.ndarray, c: np.ndarray, n, g
     return out
 
 
+def strang_composed(u0: np.ndarray, v: np.ndarray, norms2: np.ndarray, n, gamma: float, dt: float,
+                    nsteps: int, weights) -> np.ndarray:
+    """nsteps steps of S(w_s dt) ... S(w_1 dt): a composition of Strang steps (higher-order
+    splitting, named as an extension in Sec. 5); each stage is one strang_step of size w_i dt."""
+    tables = [(potential_half_phase(v, gamma, w * dt), kinetic_phase(norms2, gamma, w * dt)) for w in weights]
+    u = np.asarray(u0, dtype=np.complex128).copy()
+    for _ in range(int(nsteps)):
+        for Ph, K in tables:
+            u = strang_step(u, Ph, K, n)
+    return u
+
+
 # --------------------------------------------------------------------------
 # Observables (Sec. 3.3)
 # --------------------------------------------------------------------------

@@ -52,6 +52,7 @@ def _declare(lib):
         "lsp_plan_info": (I, [P, P]),
         "lsp_plan_paths": (I, [P, C.POINTER(C.c_int)]),
         "lsp_observables": (I, [P, P, P]),
+        "lsp_strang_composed": (I, [P, D, I64, I, P, P]),
         "lsp_plan_set_path": (I, [P, I]),
         "lsp_plan_autotune": (I, [P, D, I64, P, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "lsp_batch_create": (I, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), I]),
@@ -203,6 +204,13 @@ class Plan:
         _check(self._lib.lsp_strang_steps(self._h, float(dt), int(nsteps), _stream_ptr(stream)),
                "lsp_strang_steps")
 
+    def strang_composed(self, dt: float, nsteps: int, weights, stream=None):
+        """lsp_strang_composed: each step is S(w_s dt) ... S(w_1 dt) (e.g. fourth order with
+        weights = yoshida4())."""
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+        _check(self._lib.lsp_strang_composed(self._h, float(dt), int(nsteps), int(w.size), C.c_void_p(w.ctypes.data),
+                                             _stream_ptr(stream)), "lsp_strang_composed")
+
     def get_state(self, out=None, space: str = "physical", prec=None, stream=None):
         """Copy the state into `out` (torch CUDA tensor or numpy array).  Without `out`
         a new torch tensor on the plan's device is returned."""
@@ -303,6 +311,12 @@ class Batch:
             self.destroy()
         except Exception:
             pass
+
+
+def yoshida4():
+    """Stage weights (c, 1 - 2c, c), c = 1 / (2 - 2^(1/3)): a fourth-order composition of Strang steps."""
+    c = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    return (c, 1.0 - 2.0 * c, c)
 
 
 def strang_steps_noalloc(u, v, norm2, gamma: float, dt: float, nsteps: int, stream=None):

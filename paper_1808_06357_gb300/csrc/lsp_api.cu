@@ -684,6 +684,58 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
   return LSP_OK;
 }
 
+int lsp_strang_composed(lsp_plan p, double dt, int64_t nsteps, int nstages, const double* w, void* stream) {
+  if (!p || nsteps < 0 || !isfinite(dt) || nstages < 1 || nstages > 16 || !w) return LSP_ERR_BAD_ARG;
+  for (int i = 0; i < nstages; ++i)
+    if (!isfinite(w[i])) return LSP_ERR_BAD_ARG;
+  if (*p->err_host != 0) return *p->err_host;
+  if (nsteps == 0) return LSP_OK;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // one set of phase tables per distinct stage weight; set 0 is the plan's own
+  std::vector<double> ws;
+  std::vector<int> set_of(nstages);
+  for (int i = 0; i < nstages; ++i) {
+    int k = 0;
+    while (k < (int)ws.size() && ws[k] != w[i]) ++k;
+    if (k == (int)ws.size()) ws.push_back(w[i]);
+    set_of[i] = k;
+  }
+  const size_t tb = (size_t)p->ntot * csize(p->prec);
+  void* own[3] = {p->Ph, p->Pf, p->K};
+  std::vector<void*> extra;
+  int rc = LSP_OK;
+  for (size_t k = 1; k < ws.size() && !rc; ++k) {
+    void* b = nullptr;
+    if (cudaMallocAsync(&b, 3 * tb, s) != cudaSuccess) { cudaGetLastError(); rc = LSP_ERR_OOM; break; }
+    extra.push_back(b);
+  }
+  auto use = [&](int k) {
+    if (k == 0) { p->Ph = own[0]; p->Pf = own[1]; p->K = own[2]; }
+    else {
+      char* b = (char*)extra[k - 1];
+      p->Ph = b; p->Pf = b + tb; p->K = b + 2 * tb;
+    }
+  };
+  for (size_t k = 0; k < ws.size() && !rc; ++k) {
+    use((int)k);
+    rc = build_phase_tables(p, ws[k] * dt, s);
+  }
+  // every stage is a full Strang step of its own size (its potential half-steps are not
+  // merged with the neighbouring stage's, whose step size differs)
+  for (int64_t st = 0; st < nsteps && !rc; ++st)
+    for (int i = 0; i < nstages && !rc; ++i) {
+      use(set_of[i]);
+      rc = path_steps_on(p, p->u, 1, s);
+    }
+  use(0);
+  p->tables_valid = false;
+  for (void* b : extra) cudaFreeAsync(b, s);
+  if (rc) return rc;
+  LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return LSP_OK;
+}
+
 int lsp_observables(lsp_plan p, double* out, void* stream) {
   if (!p || !out) return LSP_ERR_BAD_ARG;
   if (*p->err_host != 0) return *p->err_host;

@@ -158,3 +158,69 @@ def test_initial_error_matches_oracle_coefficients(lib):
     e = math.sqrt(max(0.0, 1 - np.sum(np.abs(g) ** 2)) + np.sum(np.abs(g - ga) ** 2))
     assert abs(r18["e_total"] - e) < 1e-9 * e
     assert r20["e_total"] < r18["e_total"]
+
+
+@pytest.mark.parametrize("which", ["smem", "two-sweep", "four-sweep", "rank-2"])
+def test_composed_steps_match_oracle(lib, which):
+    """lsp_strang_composed (fourth-order triple of Strang steps) on every path against the oracle's
+    composition, complex128."""
+    import torch
+    inst, kw, path = {"smem": (w.c1(), {"aa": "explicit"}, None), "two-sweep": (w.c2(16), {}, None),
+                      "four-sweep": (w.c2(20), {}, 3), "rank-2": (w.c5(10, 8, 16, 6), {}, None)}[which]
+    if kw.get("aa") == "explicit":
+        kw = {"aa": "explicit", "index_set": inst.index_set}
+        norms = L.explicit_norms(inst.index_set, inst.Z, inst.n)
+    else:
+        norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    P = L.lattice_points(inst.Z, inst.n)
+    v, u0 = inst.v(P), inst.u0(P)
+    plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128", **kw)
+    if path is not None:
+        plan.set_path(path)
+    plan.set_potential(torch.from_numpy(v).cuda())
+    plan.set_state(torch.from_numpy(u0).cuda())
+    wts = lib.yoshida4()
+    plan.strang_composed(5e-3, 6, wts)
+    assert plan.status() == 0
+    ref = S.strang_composed(u0, v, norms, inst.n, inst.gamma, 5e-3, 6, wts)
+    assert rel_l2(plan.get_state().cpu().numpy(), ref) < 1e-10
+    plan.strang_steps(5e-3, 3)                       # the plan's own tables are intact afterwards
+    ref = S.strang(ref, v, norms, inst.n, inst.gamma, 5e-3, 3)
+    assert rel_l2(plan.get_state().cpu().numpy(), ref) < 1e-10
+
+
+def test_composed_fourth_order_small_lattice(lib):
+    """On the n = 55 lattice where the oracle's composed step is pinned to fourth order against the
+    exact semi-discrete propagator, the GPU composition equals the oracle's at every step size."""
+    import torch
+    Z, n = np.array([1, 34]), (55,)
+    P = L.lattice_points(Z, n)
+    norms, _ = L.minl2_norms_dp(Z, n)
+    v, u0 = w.v_smooth(P), w.gaussian_packet(P, 0.2, [0.5, 0.5], k0=1)
+    plan = lib.Plan(Z, n, 0.5, prec="c128")
+    plan.set_potential(torch.from_numpy(v).cuda())
+    for m in (80, 160, 320):
+        plan.set_state(torch.from_numpy(u0).cuda())
+        plan.strang_composed(1.0 / m, m, lib.yoshida4())
+        ref = S.strang_composed(u0, v, norms, n, 0.5, 1.0 / m, m, lib.yoshida4())
+        assert rel_l2(plan.get_state().cpu().numpy(), ref) < 1e-11
+
+
+def test_time_dependent_potential_by_steps(lib):
+    """A time-dependent potential v(x, t) = v1(x) (1 + 0.5 sin 2 pi t) (extension named in Sec. 5):
+    one lsp_strang_steps call per step with the potential at the step's midpoint, against the
+    oracle doing the same."""
+    import torch
+    inst = w.c2(16)
+    P = L.lattice_points(inst.Z, inst.n)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    v1, u0 = w.v_smooth(P), inst.u0(P)
+    plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128")
+    plan.set_state(torch.from_numpy(u0).cuda())
+    dt, u = 1e-2, u0.copy()
+    for k in range(20):
+        vk = v1 * (1 + 0.5 * np.sin(2 * np.pi * (k + 0.5) * dt))
+        plan.set_potential(torch.from_numpy(vk).cuda())
+        plan.strang_steps(dt, 1)
+        u = S.strang(u, vk, norms, inst.n, inst.gamma, dt, 1)
+    assert rel_l2(plan.get_state().cpu().numpy(), u) < 1e-11

@@ -296,3 +296,33 @@ def test_c5_small_norm_vectors_are_their_bins_representatives():
     xi = L.residues(HC, inst.Z, inst.n)
     keys = xi[:, 0] * inst.n[1] + xi[:, 1]
     assert np.unique(keys).size == HC.shape[0]
+
+
+def test_composed_strang_single_weight_is_strang():
+    Z, n = np.array([1, 7, 11]), (64,)
+    dp, H, P = _setup(Z, n)
+    u0 = w.gaussian_packet(P, 0.2, [0.5] * 3)
+    v = w.v_smooth(P)
+    a = S.strang_composed(u0, v, dp, n, 0.3, 0.01, 7, [1.0])
+    b = S.strang(u0, v, dp, n, 0.3, 0.01, 7)
+    assert np.allclose(a, b, rtol=0, atol=1e-14)
+
+
+def test_composed_strang_fourth_order_against_dense_propagator():
+    """The triple (c, 1 - 2c, c), c = 1/(2 - 2^(1/3)), converges with O(dt^4) to the exact
+    semi-discrete propagator exp(-i (W/gamma + gamma D/2) t) (dense eigen-decomposition, n = 55)."""
+    Z, n = np.array([1, 34]), (55,)
+    gamma, T = 0.5, 1.0
+    F, D, W, H, P, dp = _dense_ops(Z, n, w.v_smooth, gamma)
+    lam, Q = np.linalg.eigh(W / gamma + gamma * D / 2)
+    u0 = w.gaussian_packet(P, 0.2, [0.5, 0.5], k0=1)
+    exact = F.conj().T @ (Q @ (np.exp(-1j * lam * T) * (Q.conj().T @ (F @ u0))))      # F is unitary
+    c = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    errs = []
+    for m in (80, 160, 320):                       # dt |lambda|_max <= 2.3: the asymptotic range
+        u = S.strang_composed(u0, w.v_smooth(P), dp, n, gamma, T / m, m, [c, 1 - 2 * c, c])
+        errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert errs[-1] < 1e-6
+    for r in ratios:
+        assert 13 < r < 19, (errs, ratios)
