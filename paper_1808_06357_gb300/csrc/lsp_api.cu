@@ -149,6 +149,30 @@ __global__ void build_klut(T* lut, int count, double turns_k) {
     encode_phase(turns_k * (double)m, &lut[m]);
 }
 
+// Bin chi held at position i of the K sweep's native order (identity for the SMEM path).
+__device__ __forceinline__ long long native_bin(long long i, int order, int logN1, int logN2) {
+  if (order == kPathMultipass) {                     // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
+    long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
+    return xi2 + (xi1 << logN2);
+  }
+  if (order == kPathRank2) {
+    // n1 = A B (A = 2^ceil(m1/2)): position (e + A g) n2 + xi2 <- bin (g + B e) n2 + xi2
+    const int la = (logN1 + 1) / 2, lb = logN1 - la;
+    long long xi2 = i & ((1ll << logN2) - 1), row = i >> logN2;
+    long long e = row & ((1ll << la) - 1), g = row >> la;
+    return ((g + (e << lb)) << logN2) + xi2;
+  }
+  if (order == kPathRank1x4) {
+    // N2 = A B (A = 2^ceil(log2 N2 / 2)): position xi1 + N1 (e + A g) <- bin (g + B e) + N2 xi1
+    const int la = (logN2 + 1) / 2, lb = logN2 - la;
+    long long xi1 = i & ((1ll << logN1) - 1), row = i >> logN1;
+    long long e = row & ((1ll << la) - 1), g = row >> la;
+    return (g + (e << lb)) + (xi1 << logN2);
+  }
+  return i;
+}
+
+// K (skipped when K == nullptr: the kernels then take K from klut through kidx)
 template <typename T>
 __global__ void build_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf, T* K,
                              const T* __restrict__ klut, long long n, double turns_v, double turns_k, int order,
@@ -157,29 +181,22 @@ __global__ void build_tables(const double* __restrict__ v, const int32_t* __rest
     double th = v[i] * turns_v;                       // -dt v / (4 pi gamma): half step, in turns
     T a, b, c;
     encode_phase_pair(th, &a, &b);
-    long long bin = i;
-    if (order == kPathMultipass) {                     // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
-      long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
-      bin = xi2 + (xi1 << logN2);
-    } else if (order == kPathRank2) {
-      // n1 = A B (A = 2^ceil(m1/2)): position (e + A g) n2 + xi2 <- bin (g + B e) n2 + xi2
-      const int la = (logN1 + 1) / 2, lb = logN1 - la;
-      long long xi2 = i & ((1ll << logN2) - 1), row = i >> logN2;
-      long long e = row & ((1ll << la) - 1), g = row >> la;
-      bin = ((g + (e << lb)) << logN2) + xi2;
-    } else if (order == kPathRank1x4) {
-      // N2 = A B (A = 2^ceil(log2 N2 / 2)): position xi1 + N1 (e + A g) <- bin (g + B e) + N2 xi1
-      const int la = (logN2 + 1) / 2, lb = logN2 - la;
-      long long xi1 = i & ((1ll << logN1) - 1), row = i >> logN1;
-      long long e = row & ((1ll << la) - 1), g = row >> la;
-      bin = (g + (e << lb)) + (xi1 << logN2);
-    }
-    if (klut) c = klut[norm2[bin]];
-    else encode_phase(turns_k * (double)norm2[bin], &c);
     Ph[i] = a;
     Pf[i] = b;
-    K[i] = c;
+    if (K) {
+      const long long bin = native_bin(i, order, logN1, logN2);
+      if (klut) c = klut[norm2[bin]];
+      else encode_phase(turns_k * (double)norm2[bin], &c);
+      K[i] = c;
+    }
   }
+}
+
+// ||h||^2 of the bin at each native position, as a byte (four-sweep paths, max ||h||^2 < 256).
+__global__ void build_kidx(const int32_t* __restrict__ norm2, uint8_t* kidx, long long n, int order, int logN1,
+                           int logN2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    kidx[i] = (uint8_t)norm2[native_bin(i, order, logN1, logN2)];
 }
 
 template <typename S, typename D> __device__ __forceinline__ D cvt(S x);
@@ -248,15 +265,16 @@ int build_phase_tables(lsp_plan p, double dt, cudaStream_t s) {
   const double turns_k = -M_PI * p->gamma * dt;
   const int order = p->path;
   const int nlut = p->klut ? (int)p->max_norm2 + 1 : 0;
+  void* K = p->kidx ? nullptr : p->K;                      // four-sweep paths read K through kidx
   if (p->prec == LSP_C64) {
     if (nlut) build_klut<float2><<<(nlut + 255) / 256, 256, 0, s>>>((float2*)p->klut, nlut, turns_k);
     build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
-                                                            (float2*)p->K, (const float2*)p->klut, p->ntot, turns_v,
+                                                            (float2*)K, (const float2*)p->klut, p->ntot, turns_v,
                                                             turns_k, order, p->logN1, p->logN2);
   } else {
     if (nlut) build_klut<double2><<<(nlut + 255) / 256, 256, 0, s>>>((double2*)p->klut, nlut, turns_k);
     build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
-                                                              (double2*)p->K, (const double2*)p->klut, p->ntot,
+                                                              (double2*)K, (const double2*)p->klut, p->ntot,
                                                               turns_v, turns_k, order, p->logN1, p->logN2);
   }
   return cuda_status(cudaGetLastError());
@@ -348,8 +366,8 @@ static void free_plan(lsp_plan p) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
-  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->klut, p->tw_line, p->tw_fine, p->tw_coarse,
-                  p->tw_pass, p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
+  void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->klut, p->kidx, p->tw_line, p->tw_fine,
+                  p->tw_coarse, p->tw_pass, p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
   for (void* b : bufs) if (b) cudaFree(b);
   if (p->err_host) cudaFreeHost(p->err_host);
   cudaSetDevice(prev);
@@ -374,6 +392,8 @@ static int upload(lsp_plan p, void** dst, const std::vector<unsigned char>& host
   return cudaMemcpy(*dst, host.data(), host.size(), cudaMemcpyHostToDevice) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
 }
 
+static int setup_kidx(lsp_plan p);
+
 // Can plan p run on execution path `path`?
 static bool path_available(lsp_plan p, int path) {
   const size_t sz = csize(p->prec);
@@ -392,7 +412,7 @@ static bool path_available(lsp_plan p, int path) {
 
 // Geometry, twiddle tables (FP64 evaluation, rounded once) and kernel
 // descriptors of execution path `path`; the previous path's tables are freed.
-static int setup_path(lsp_plan p, int path) {
+static int setup_path_tables(lsp_plan p, int path) {
   void** olds[] = {&p->tw_line, &p->tw_fine, &p->tw_coarse, &p->tw_pass, &p->tw_small};
   for (void** b : olds)
     if (*b) { cudaFree(*b); *b = nullptr; }
@@ -489,6 +509,29 @@ static int setup_path(lsp_plan p, int path) {
   p->N1 = (int)p->n[p->r - 1];
   p->N2 = p->r == 2 ? (int)p->n[0] : 1;
   return small_upload_desc(p, 0);
+}
+
+// The byte index of K for the four-sweep paths (when every ||h||^2 fits in a byte and the
+// norms are known); otherwise the paths read the K table.
+static int setup_kidx(lsp_plan p) {
+  const bool want = (p->path == kPathRank2 || p->path == kPathRank1x4) && p->klut && p->max_norm2 < kKIdxMax;
+  if (!want) {
+    if (p->kidx) { cudaFree(p->kidx); p->kidx = nullptr; }
+    return LSP_OK;
+  }
+  if (!p->kidx) {
+    int rc = dalloc(p, &p->kidx, (size_t)p->ntot);
+    if (rc) return rc;
+  }
+  build_kidx<<<grid_for(p->ntot), 256>>>(p->norm2, p->kidx, p->ntot, p->path, p->logN1, p->logN2);
+  return cuda_status(cudaDeviceSynchronize());
+}
+
+// setup_path_tables, then (once the norms are known) the K byte index in the new path's order
+static int setup_path(lsp_plan p, int path) {
+  int rc = setup_path_tables(p, path);
+  if (!rc && p->norms_ready) rc = setup_kidx(p);
+  return rc;
 }
 
 int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
@@ -627,6 +670,8 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
     p->max_norm2 = mx;
   }
   if (p->max_norm2 < kKLutMax && (rc = dalloc(p, &p->klut, (p->max_norm2 + 1) * sz))) return fail(rc);
+  p->norms_ready = true;
+  if ((rc = setup_kidx(p))) return fail(rc);
 
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSP_ERR_CUDA);
   *out = p;
@@ -702,19 +747,20 @@ int lsp_strang_composed(lsp_plan p, double dt, int64_t nsteps, int nstages, cons
     set_of[i] = k;
   }
   const size_t tb = (size_t)p->ntot * csize(p->prec);
-  void* own[3] = {p->Ph, p->Pf, p->K};
+  const size_t lb = p->klut ? ((size_t)p->max_norm2 + 1) * csize(p->prec) : 0;
+  void* own[4] = {p->Ph, p->Pf, p->K, p->klut};
   std::vector<void*> extra;
   int rc = LSP_OK;
   for (size_t k = 1; k < ws.size() && !rc; ++k) {
     void* b = nullptr;
-    if (cudaMallocAsync(&b, 3 * tb, s) != cudaSuccess) { cudaGetLastError(); rc = LSP_ERR_OOM; break; }
+    if (cudaMallocAsync(&b, 3 * tb + lb, s) != cudaSuccess) { cudaGetLastError(); rc = LSP_ERR_OOM; break; }
     extra.push_back(b);
   }
   auto use = [&](int k) {
-    if (k == 0) { p->Ph = own[0]; p->Pf = own[1]; p->K = own[2]; }
+    if (k == 0) { p->Ph = own[0]; p->Pf = own[1]; p->K = own[2]; p->klut = own[3]; }
     else {
       char* b = (char*)extra[k - 1];
-      p->Ph = b; p->Pf = b + tb; p->K = b + 2 * tb;
+      p->Ph = b; p->Pf = b + tb; p->K = b + 2 * tb; p->klut = lb ? b + 3 * tb : nullptr;
     }
   };
   for (size_t k = 0; k < ws.size() && !rc; ++k) {

@@ -29,6 +29,8 @@ constexpr int kSmallSmemBytes = 200 * 1024;
 constexpr int kSmallThreads = 512;
 // Largest ||h||^2 for which K is tabulated per norm value.
 constexpr long long kKLutMax = 1ll << 20;
+// The four-sweep kernels read K as klut[kidx[i]] (one byte per point) below this norm.
+constexpr long long kKIdxMax = 256;
 // Bounded device-side waits (grid barrier): spins of ~100 ns each.
 constexpr long long kSpinLimit = 1ll << 25;
 
@@ -78,6 +80,8 @@ struct lsp_plan_s {
   void* Pf = nullptr;         // exp(-i dt v / gamma), kappa order, encoded
   void* K = nullptr;          // exp(-i gamma 2 pi^2 |h|^2 dt) in the kernel's bin order
   void* klut = nullptr;       // K per value of ||h||^2 = 0..max_norm2 (when max_norm2 < kKLutMax)
+  uint8_t* kidx = nullptr;    // four-sweep paths: ||h||^2 in the K sweep's native order (max_norm2 < kKIdxMax)
+  bool norms_ready = false;   // norm2 / max_norm2 computed
   void* tw_line = nullptr;    // W_Lmax^k, k < Lmax (two-sweep); W_{2^M1}^k (four-sweep: n1 or N2 points)
   void* tw_fine = nullptr;    // W_n^k, k < n / Lmax (two-sweep); W_n^k, k < N2 (rank-1 four-sweep)
   void* tw_coarse = nullptr;  // W_N1^k, k < N1 (rank-1 four-sweep)

@@ -55,6 +55,9 @@ template <typename T> struct S4Inst {
   const T* tw_bf;     // rank-1: W_n^k, k < N2 (fine factor)
   double2* spec;      // spectral output (chi order)
   int* err;           // sticky device error word
+  const uint8_t* kidx;  // K sweeps: ||h||^2 per native position (null: read K)
+  const T* klut;        // K per value of ||h||^2, nlut entries (<= 256)
+  int nlut;
   R inv_n;
 };
 
@@ -149,7 +152,8 @@ __device__ __forceinline__ T big_twiddle(const S4Inst<T>& I, unsigned k1, unsign
   return twprod(__ldg(I.tw_bl + (c >> M1)), __ldg(I.tw_bf + (c & ((1u << M1) - 1u))));
 }
 
-template <typename T, int M1, int M2, int KIND>
+// KIDX (K sweeps only): K comes from klut[kidx[i]] (one byte per point) instead of the K table.
+template <typename T, int M1, int M2, int KIND, bool KIDX = false>
 __global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MINB_2T : S4Cfg<T>::MINB)
     sweep4(const __grid_constant__ S4Inst<T> I) {
   using Ops = S4Ops<KIND>;
@@ -160,6 +164,12 @@ __global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MIN
   extern __shared__ __align__(128) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const T* tw_line = Geo::ROW ? I.tw_rows : Geo::SWEEP_A ? I.tw_b : I.tw_a;
+  // K sweeps: K from a table of at most 256 values indexed by one byte per point
+  __shared__ T klut[Ops::KIN && KIDX ? 256 : 1];
+  if constexpr (Ops::KIN && KIDX) {
+    for (int i = threadIdx.x; i < I.nlut; i += Geo::NT) klut[i] = I.klut[i];
+    __syncthreads();
+  }
 
   for (int t = blockIdx.x; t < Geo::NTILES; t += gridDim.x) {
     int outer, c0;
@@ -210,8 +220,18 @@ __global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MIN
     // ---- forward half: pass-1 pattern in, natural order out ----
     // K is loaded before the transform so that its latency hides behind it (measured: a
     // quarter of the four-sweep step's time at 2^22 when loaded after the transform)
-    T kv[16];
-    if constexpr (Ops::KIN) {
+    T kv[KIDX ? 1 : 16];
+    unsigned kb[4];                                       // 16 byte indices, packed
+    if constexpr (Ops::KIN && KIDX) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        unsigned x = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          x |= (unsigned)__ldcs(I.kidx + base + Geo::off(bn, jn + ((4 * w + t) << (LOGL - 4)))) << (8 * t);
+        kb[w] = x;
+      }
+    } else if constexpr (Ops::KIN) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + base + Geo::off(bn, jn + (q << (LOGL - 4))));
     }
@@ -226,8 +246,13 @@ __global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MIN
         v[q] = twmul(v[q], big_twiddle<T, M1, M2>(I, c0 + bn, outer + ((jn + (q << (LA - 4))) << LB)));
     }
     if constexpr (Ops::KIN) {
+      if constexpr (KIDX) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
+        for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], klut[(kb[q >> 2] >> (8 * (q & 3))) & 255u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
+      }
       G::idft(sm, tw_line, v);
     }
     if constexpr (Ops::SPEC) {
@@ -265,6 +290,7 @@ __global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MIN
 // count of each geometry (rows, A / X, B / Y).
 struct S4Kernels {
   const void* k[kS4Kinds] = {};
+  const void* k_kidx = nullptr;   // the K sweep reading K through kidx
   int ntiles[3] = {};
 };
 
@@ -279,6 +305,7 @@ template <typename T, int M1, int M2, bool RANK1> S4Kernels s4_kernels() {
     K.k[kR2AInv] = (const void*)sweep4<T, M1, M2, kR2AInv>;
     K.k[kR2B] = (const void*)sweep4<T, M1, M2, kR2B>;
     K.k[kR2BFwd] = (const void*)sweep4<T, M1, M2, kR2BFwd>;
+    K.k_kidx = (const void*)sweep4<T, M1, M2, kR2B, true>;
     K.ntiles[0] = S4Geo<T, M1, M2, kR2Mid>::NTILES;
     K.ntiles[1] = S4Geo<T, M1, M2, kR2A>::NTILES;
     K.ntiles[2] = S4Geo<T, M1, M2, kR2B>::NTILES;
@@ -291,6 +318,7 @@ template <typename T, int M1, int M2, bool RANK1> S4Kernels s4_kernels() {
     K.k[kYInv] = (const void*)sweep4<T, M1, M2, kYInv>;
     K.k[kZ] = (const void*)sweep4<T, M1, M2, kZ>;
     K.k[kZFwd] = (const void*)sweep4<T, M1, M2, kZFwd>;
+    K.k_kidx = (const void*)sweep4<T, M1, M2, kZ, true>;
     K.ntiles[0] = S4Geo<T, M1, M2, kZ>::NTILES;
     K.ntiles[1] = S4Geo<T, M1, M2, kXMid>::NTILES;
     K.ntiles[2] = S4Geo<T, M1, M2, kY>::NTILES;

@@ -43,6 +43,9 @@ template <typename T> static S4Inst<T> s4_inst(lsp_plan p, void* state) {
   I.tw_bf = (const T*)p->tw_fine;
   I.spec = (double2*)p->stage;
   I.err = p->err;
+  I.kidx = p->kidx;
+  I.klut = (const T*)p->klut;
+  I.nlut = p->klut ? (int)p->max_norm2 + 1 : 0;
   I.inv_n = (decltype(I.inv_n))(1.0 / (double)p->ntot);
   return I;
 }
@@ -92,9 +95,10 @@ template <typename T> static int s4_steps_impl(lsp_plan p, void* state, int64_t 
   const int seq[3] = {r2 ? kR2A : kY, r2 ? kR2B : kZ, r2 ? kR2AInv : kYInv};
   const int geo[3] = {r2 ? 1 : 2, r2 ? 2 : 0, r2 ? 1 : 2};
   int rc = LSP_OK;
+  const void* kin = I.kidx ? K.k_kidx : K.k[seq[1]];                // the K sweep
   for (int64_t st = 0; st < nsteps && !rc; ++st) {
     rc = s4_launch<T>(K.k[st == 0 ? head : mid], I, K.ntiles[pg], s);
-    for (int i = 0; i < 3 && !rc; ++i) rc = s4_launch<T>(K.k[seq[i]], I, K.ntiles[geo[i]], s);
+    for (int i = 0; i < 3 && !rc; ++i) rc = s4_launch<T>(i == 1 ? kin : K.k[seq[i]], I, K.ntiles[geo[i]], s);
   }
   if (!rc) rc = s4_launch<T>(K.k[tail], I, K.ntiles[pg], s);
   return rc;
