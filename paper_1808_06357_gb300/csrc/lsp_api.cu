@@ -370,6 +370,8 @@ static void free_plan(lsp_plan p) {
                   p->tw_coarse, p->tw_pass, p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
   for (void* b : bufs) if (b) cudaFree(b);
   if (p->err_host) cudaFreeHost(p->err_host);
+  if (p->s4_graph) cudaGraphExecDestroy(p->s4_graph);
+  if (p->capture) cudaStreamDestroy(p->capture);
   cudaSetDevice(prev);
   delete p;
 }

@@ -99,6 +99,11 @@ struct lsp_plan_s {
 
   int dp_box = 0;
   int64_t max_norm2 = 0;
+  // four-sweep paths: the launch sequence of the last call, captured as a CUDA graph and
+  // replayed while the call's parameters are unchanged (key: nsteps and the kernel arguments)
+  cudaGraphExec_t s4_graph = nullptr;
+  std::vector<unsigned char> s4_graph_key;
+  cudaStream_t capture = nullptr;   // private stream for graph capture
   double tables_dt = 0.0;     // dt of the current phase tables (NaN: none)
   bool tables_valid = false;
 };

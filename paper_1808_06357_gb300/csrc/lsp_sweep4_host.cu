@@ -1,6 +1,8 @@
 // Host side of the four-sweep Strang step (rank-2 lattices, and rank-1
 // lattices on the four-sweep schedule): descriptors, launches, step driver,
 // spectral output.
+#include <string.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -84,10 +86,9 @@ template <typename T> static int s4_launch(const void* fn, const S4Inst<T>& I, i
 
 // N steps: P-sweep head, then per step the three other sweeps and the next
 // P-sweep (mid), and the P-sweep tail.  Sweep geometries: rows (0), A / X (1), B / Y (2).
-template <typename T> static int s4_steps_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+template <typename T> static int s4_launch_steps(lsp_plan p, const S4Inst<T>& I, int64_t nsteps, cudaStream_t s) {
   S4Kernels K;
   if (!s4_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
-  const S4Inst<T> I = s4_inst<T>(p, state);
   const bool r2 = p->path == kPathRank2;
   // kernel, geometry of each sweep of a step in order
   const int head = r2 ? kR2Head : kXHead, mid = r2 ? kR2Mid : kXMid, tail = r2 ? kR2Tail : kXTail;
@@ -102,6 +103,42 @@ template <typename T> static int s4_steps_impl(lsp_plan p, void* state, int64_t 
   }
   if (!rc) rc = s4_launch<T>(K.k[tail], I, K.ntiles[pg], s);
   return rc;
+}
+
+constexpr int64_t kGraphMinSteps = 16;
+
+// The 4 N + 1 launches of a call, captured once as a CUDA graph on a private
+// stream and replayed on the caller's stream while (nsteps, kernel arguments) are
+// unchanged: the sweeps then follow one another without per-launch host work.
+template <typename T> static int s4_steps_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  const S4Inst<T> I = s4_inst<T>(p, state);
+  if (nsteps < kGraphMinSteps) return s4_launch_steps<T>(p, I, nsteps, s);   // short calls (adjoint, stages)
+  std::vector<unsigned char> key(sizeof(I) + sizeof(nsteps) + sizeof(int));
+  memcpy(key.data(), &I, sizeof(I));
+  memcpy(key.data() + sizeof(I), &nsteps, sizeof(nsteps));
+  memcpy(key.data() + sizeof(I) + sizeof(nsteps), &p->path, sizeof(int));
+  if (!p->s4_graph || key != p->s4_graph_key) {
+    if (p->s4_graph) { cudaGraphExecDestroy(p->s4_graph); p->s4_graph = nullptr; }
+    if (!p->capture) LSP_CUDA_TRY(cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking));
+    // kernel attributes and grid sizes are set and cached before the capture
+    S4Kernels K;
+    if (!s4_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
+    int grid = 0, rc = LSP_OK;
+    for (const void* fn : K.k)
+      if (fn && (rc = s4_grid(fn, S4Cfg<T>::NT, (size_t)S4Cfg<T>::TILE * sizeof(T), &grid))) return rc;
+    if (K.k_kidx && (rc = s4_grid(K.k_kidx, S4Cfg<T>::NT, (size_t)S4Cfg<T>::TILE * sizeof(T), &grid))) return rc;
+    LSP_CUDA_TRY(cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal));
+    rc = s4_launch_steps<T>(p, I, nsteps, p->capture);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->capture, &g);
+    if (rc || ec != cudaSuccess) { if (g) cudaGraphDestroy(g); return rc ? rc : LSP_ERR_CUDA; }
+    const cudaError_t ei = cudaGraphInstantiate(&p->s4_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { p->s4_graph = nullptr; return LSP_ERR_CUDA; }
+    p->s4_graph_key = key;
+  }
+  LSP_CUDA_TRY(cudaGraphLaunch(p->s4_graph, s));
+  return LSP_OK;
 }
 
 // Spectral coefficients of the current state into p->stage (chi order, c128),
