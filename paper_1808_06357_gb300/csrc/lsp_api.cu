@@ -311,7 +311,7 @@ static void factorize(int len, SmallAxis& ax) {
 template <typename T> static T table_entry(double f) {
   using R = decltype(T{}.x);
   const double ang = -2.0 * M_PI * f;
-  if (LSP_TW_WM1 && sizeof(R) == sizeof(float)) {
+  if (sizeof(R) == sizeof(float)) {
     const double sh = sin(M_PI * f);
     return T{(R)(-2.0 * sh * sh), (R)sin(ang)};
   }

@@ -160,10 +160,6 @@ template <typename T> __device__ __forceinline__ T cmulc(T a, T b) {
 // same four FMAs as a complex multiply; rounding cos t itself would leave
 // |w| > 1 for every small angle and bias the norm a little every step.
 // complex128 tables hold w = (cos t, sin t).
-#ifndef LSP_TW_WM1
-#define LSP_TW_WM1 1
-#endif
-#if LSP_TW_WM1
 __device__ __forceinline__ float2 twmul(float2 x, float2 m) {
   return make_float2(fmaf(x.x, m.x, fmaf(-x.y, m.y, x.x)), fmaf(x.x, m.y, fmaf(x.y, m.x, x.y)));
 }
@@ -174,17 +170,6 @@ __device__ __forceinline__ float2 twmulc(float2 x, float2 m) {   // x conj(1 + m
 __device__ __forceinline__ float2 twprod(float2 a, float2 b) {
   return make_float2(a.x + b.x + fmaf(a.x, b.x, -a.y * b.y), a.y + b.y + fmaf(a.x, b.y, a.y * b.x));
 }
-#else
-__device__ __forceinline__ float2 twmul(float2 x, float2 w) {
-  return make_float2(fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x));
-}
-__device__ __forceinline__ float2 twmulc(float2 x, float2 w) {
-  return make_float2(fmaf(x.x, w.x, x.y * w.y), fmaf(x.y, w.x, -x.x * w.y));
-}
-__device__ __forceinline__ float2 twprod(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-#endif
 // a * (DIR * i):  DIR = -1 -> -i,  DIR = +1 -> +i
 template <int DIR, typename T> __device__ __forceinline__ T cmul_i(T a) {
   return DIR < 0 ? cmake(a.y, -a.x) : cmake(-a.y, a.x);

@@ -70,9 +70,6 @@ template <typename T> struct Cfg;
 #ifndef LSP_MP_TW_SMEM
 #define LSP_MP_TW_SMEM 1
 #endif
-#ifndef LSP_MP_SWEEPS
-#define LSP_MP_SWEEPS 0
-#endif
 template <> struct Cfg<float2> {
   static constexpr int NT = LSP_MP_NT_C64, NW = 1, TILE = 16 * NT, MINB = LSP_MINB_C64;
 };
@@ -476,10 +473,6 @@ template <typename T, int M> MPKernels mp_kernels_for() {
   MPKernels k;
   k.persistent = (const void*)mp_persistent<T, NT, M>;
   k.persistent_smem = SmemLayout<T, M>::bytes;
-#if LSP_MP_SWEEPS
-  k.sweep[kMid] = (const void*)mp_sweep<T, NT, M, kMid>;
-  k.sweep[kRow] = (const void*)mp_sweep<T, NT, M, kRow>;
-#endif
   k.sweep[kHead] = (const void*)mp_sweep<T, NT, M, kHead>;
   k.sweep[kTail] = (const void*)mp_sweep<T, NT, M, kTail>;
   k.sweep[kColFwd] = (const void*)mp_sweep<T, NT, M, kColFwd>;

@@ -119,21 +119,11 @@ int multipass_upload_desc(lsp_plan p, cudaStream_t s) {
   return p->prec == LSP_C64 ? upload_desc_impl<float2>(p, s) : upload_desc_impl<double2>(p, s);
 }
 
-// Sweeps 1..2N-1 of N steps (row, mid, ..., row): one persistent cooperative
-// launch, or (LSP_MP_SWEEPS) one launch per sweep.
+// Sweeps 1..2N-1 of N steps (row, mid, ..., row): one persistent cooperative launch.
 template <typename T>
 static int middle_sweeps(int m, const MPInst<T>* d, const int2* colmap, const int2* rowmap, int ninst, int total_col,
                          int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
-#if LSP_MP_SWEEPS
-  int rc = LSP_OK;
-  for (int64_t k = 0; k < nsteps && !rc; ++k) {
-    rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kRow, s);
-    if (!rc && k + 1 < nsteps) rc = launch_sweep<T>(m, d, colmap, rowmap, ninst, total_col, total_row, kMid, s);
-  }
-  return rc;
-#else
   return launch_persistent<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
-#endif
 }
 
 // head sweep, sweeps 1..2N-1, tail sweep
