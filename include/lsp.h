@@ -223,8 +223,9 @@ int lsp_plan_set_path(lsp_plan p, int path);
 
 /*
  * lsp_plan_autotune -- time `nsteps` Strang steps of size dt on every
- * available path, on a scratch copy of the state (the plan's state is not
- * changed), and keep the fastest.  Not in the paper: a schedule choice.
+ * available path (after one untimed call of the same length), on a scratch
+ * copy of the state (the plan's state is not changed), and keep the fastest.
+ * Not in the paper: a schedule choice.
  *   chosen  receives the kept path (may be NULL).
  *   ms      NULL, or 4 doubles receiving each path's time in ms (-1: not available).
  * Synchronises `stream`.  Errors: BAD_ARG, OOM, CUDA, TIMEOUT (then the plan

@@ -952,7 +952,9 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
     if (c != p->path && (rc = setup_path(p, c))) break;
     if ((rc = build_phase_tables(p, dt, s))) break;
     if (cudaMemcpyAsync(scratch, p->u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
-    if ((rc = path_steps_on(p, scratch, 2, s))) break;            // warm-up: every kernel of the path once
+    // warm-up with the timed call itself: every kernel of the path runs once and a
+    // four-sweep path captures its launch graph outside the timed region
+    if ((rc = path_steps_on(p, scratch, nsteps, s))) break;
     cudaEventRecord(e0, s);
     if ((rc = path_steps_on(p, scratch, nsteps, s))) break;
     cudaEventRecord(e1, s);
