@@ -4,8 +4,11 @@
 //  * multipass instances: one group per lattice size 2^m (kernels are
 //    specialised per size); each group is a head sweep, one persistent
 //    cooperative launch over the tiles of all its instances, and a tail sweep;
-//  * four-sweep instances (rank-2, and rank-1 beyond the two-sweep sizes;
-//    2^24 points and more, each enough to fill the GPU): stepped one after another.
+//  * rank-1 four-sweep instances of up to 2^22 points: one group per (size, K
+//    form); each sweep is one launch over the tiles of all the group's instances,
+//    and a call of 16 steps or more replays the groups' launches as a CUDA graph;
+//  * other four-sweep instances (rank-2, larger rank-1; each fills the GPU by
+//    itself): stepped one after another.
 // Each instance's phase tables are built with its own dt on every call.
 #include <string.h>
 
@@ -34,10 +37,51 @@ void free_batch(lsp_batch b) {
     cudaFree(c.colmap);
     cudaFree(c.rowmap);
   }
+  for (auto& c : b->s4classes) s4_class_free(c);
+  if (b->s4_graph) cudaGraphExecDestroy(b->s4_graph);
+  if (b->capture) cudaStreamDestroy(b->capture);
   cudaFree(b->bar);
   cudaFree(b->err);
   if (b->err_host) cudaFreeHost(b->err_host);
   delete b;
+}
+
+constexpr int64_t kGraphMinSteps = 16;
+
+// The four-sweep groups' launches of one call: direct for short calls, else a CUDA
+// graph captured on a private stream while (nsteps, descriptors) are unchanged.
+int s4_batch_steps(lsp_batch b, int64_t nsteps, cudaStream_t s) {
+  std::vector<unsigned char> key(sizeof(nsteps));
+  memcpy(key.data(), &nsteps, sizeof(nsteps));
+  for (auto& c : b->s4classes) {
+    bool changed = false;
+    int rc = s4_class_sync(c, b->plans, &changed);
+    if (rc) return rc;
+    key.insert(key.end(), c.inst_host.begin(), c.inst_host.end());
+  }
+  auto launch_all = [&](cudaStream_t st) {
+    for (auto& c : b->s4classes) {
+      int rc = s4_class_steps(c, b->prec, nsteps, st);
+      if (rc) return rc;
+    }
+    return (int)LSP_OK;
+  };
+  if (nsteps < kGraphMinSteps) return launch_all(s);
+  if (!b->s4_graph || key != b->s4_graph_key) {
+    if (b->s4_graph) { cudaGraphExecDestroy(b->s4_graph); b->s4_graph = nullptr; }
+    if (!b->capture) LSP_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+    LSP_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_all(b->capture);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->capture, &g);
+    if (rc || ec != cudaSuccess) { if (g) cudaGraphDestroy(g); return rc ? rc : LSP_ERR_CUDA; }
+    const cudaError_t ei = cudaGraphInstantiate(&b->s4_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { b->s4_graph = nullptr; return LSP_ERR_CUDA; }
+    b->s4_graph_key = key;
+  }
+  LSP_CUDA_TRY(cudaGraphLaunch(b->s4_graph, s));
+  return LSP_OK;
 }
 
 }  // namespace
@@ -64,10 +108,23 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   auto fail = [&](int code) { free_batch(b); return code; };
 
   std::map<int, std::vector<int>> by_m;
+  std::map<std::pair<int, bool>, std::vector<int>> by_m4;
   for (int i = 0; i < count; ++i) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
+    else if (s4_batchable(plans[i])) by_m4[{plans[i]->logn, plans[i]->kidx != nullptr}].push_back(i);
     else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4) b->seq_ids.push_back(i);
     else b->small_ids.push_back(i);
+  }
+  for (auto& kv : by_m4) {
+    b->s4classes.emplace_back();
+    lsp_batch_s::S4Class& c = b->s4classes.back();
+    c.m = kv.first.first;
+    c.kidx = kv.first.second;
+    c.ids = kv.second;
+    int rc = s4_class_init(c, b->plans);
+    bool changed = false;
+    if (!rc) rc = s4_class_sync(c, b->plans, &changed);
+    if (rc) return fail(rc);
   }
   // SMEM-resident group
   if (!b->small_ids.empty()) {
@@ -130,6 +187,10 @@ int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream)
   }
   if (!b->small_ids.empty()) {
     int rc = small_batch_launch(b->prec, b->small_desc, (int)b->small_ids.size(), b->small_max_n, nsteps, s);
+    if (rc) return rc;
+  }
+  if (!b->s4classes.empty()) {
+    int rc = s4_batch_steps(b, nsteps, s);
     if (rc) return rc;
   }
   for (int i : b->seq_ids) {     // each fills the GPU by itself

@@ -128,6 +128,20 @@ struct lsp_batch_s {
     int total_col = 0, total_row = 0;
   };
   std::vector<Class> classes;
+  // rank-1 four-sweep instances of one size (and K form): one launch per sweep for all
+  struct S4Class {
+    int m = 0;
+    bool kidx = false;           // K sweeps read K through the byte index
+    std::vector<int> ids;
+    void* inst = nullptr;        // device array of sweep descriptors
+    std::vector<unsigned char> inst_host;   // its host copy
+    int2* map[3] = {};           // launch tile -> (instance in class, local tile), per geometry
+    int total[3] = {};
+  };
+  std::vector<S4Class> s4classes;
+  cudaGraphExec_t s4_graph = nullptr;       // the four-sweep classes' launches of one call
+  std::vector<unsigned char> s4_graph_key;
+  cudaStream_t capture = nullptr;
   unsigned* bar = nullptr;       // grid-barrier counter (reused by every class)
   int* err = nullptr;            // device error word
   int* err_host = nullptr;       // pinned mirror
@@ -294,6 +308,14 @@ int multipass_batch_steps(int prec, int m, const void* ddesc, const int2* colmap
 bool s4_supports_rank2(int prec, int m1, int m2);
 bool s4_supports_rank1(int prec, int m);
 int s4_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
+// Batches of rank-1 four-sweep plans of one size (lsp_batch.cu): whether a plan has
+// multi-instance kernels; descriptor upload (sets *changed when the descriptors moved);
+// the launches of nsteps steps; release.
+bool s4_batchable(lsp_plan p);
+int s4_class_init(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans);
+int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed);
+int s4_class_steps(const lsp_batch_s::S4Class& c, int prec, int64_t nsteps, cudaStream_t s);
+void s4_class_free(lsp_batch_s::S4Class& c);
 int s4_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
 // steps of the plan's current path on a state buffer of the plan's geometry
 int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);

@@ -152,137 +152,167 @@ __device__ __forceinline__ T big_twiddle(const S4Inst<T>& I, unsigned k1, unsign
   return twprod(__ldg(I.tw_bl + (c >> M1)), __ldg(I.tw_bf + (c & ((1u << M1) - 1u))));
 }
 
-// KIDX (K sweeps only): K comes from klut[kidx[i]] (one byte per point) instead of the K table.
-template <typename T, int M1, int M2, int KIND, bool KIDX = false>
-__global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MINB_2T : S4Cfg<T>::MINB)
-    sweep4(const __grid_constant__ S4Inst<T> I) {
+// K value of byte index k from the per-norm table (shared memory, or global in batches).
+template <typename T, bool SMEM> __device__ __forceinline__ T kval(const T* lut, unsigned k) {
+  if constexpr (SMEM) return lut[k];
+  else return __ldg(lut + k);
+}
+
+// One tile of one sweep.  KIDX (K sweeps only): K comes from lut[kidx[i]] (one byte per
+// point) instead of the K table.
+template <typename T, int M1, int M2, int KIND, bool KIDX, bool LUT_SMEM>
+__device__ __forceinline__ void sweep4_tile(const S4Inst<T>& I, int t, T* sm, const T* lut) {
   using Ops = S4Ops<KIND>;
   using Geo = S4Geo<T, M1, M2, KIND>;
   using G = typename Geo::G;
   constexpr int LOGL = Geo::LOGL, LR1 = G::LOGR1, R1 = G::R1;
   constexpr int LA = Geo::LA, LB = Geo::LB;
+  const T* tw_line = Geo::ROW ? I.tw_rows : Geo::SWEEP_A ? I.tw_b : I.tw_a;
+  int outer, c0;
+  const size_t base = Geo::base(t, outer, c0);
+  T v[16];
+  int bn, jn;                                          // this thread's natural-order line and butterfly
+  G::template bm<4>(0, bn, jn);
+  if constexpr (Ops::INV_IN) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = ldst(I.u + base + Geo::off(bn, jn + (q << (LOGL - 4))));
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[q * R1 + r] = ldst(I.u + base + Geo::off(b, j + (r << (LOGL - LR1))));
+    }
+  }
+  __syncthreads();                                     // previous tile's exchange reads done
+
+  // ---- inverse half: natural order in, pass-1 pattern out ----
+  if constexpr (Ops::CONJ_COL) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = twmulc(v[q], __ldg(I.tw_col + outer * (jn + (q << (LB - 4)))));
+  }
+  if constexpr (Ops::CONJ_BIG) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      v[q] = twmulc(v[q], big_twiddle<T, M1, M2>(I, c0 + bn, outer + ((jn + (q << (LA - 4))) << LB)));
+  }
+  if constexpr (Ops::INV_IN) G::idft(sm, tw_line, v);
+
+  // ---- physical samples: 1/n and the potential phase ----
+  if constexpr (Ops::HAS_P) {
+    const T* P = Ops::FULL_P ? I.Pf : I.Ph;
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        T x = v[q * R1 + r];
+        if constexpr (Ops::INV_IN) x = cscale(x, I.inv_n);
+        v[q * R1 + r] = apply_phase(x, ldtab(P + base + Geo::off(b, j + (r << (LOGL - LR1)))));
+      }
+    }
+  }
+
+  // ---- forward half: pass-1 pattern in, natural order out ----
+  // K is loaded before the transform so that its latency hides behind it (measured: a
+  // quarter of the four-sweep step's time at 2^22 when loaded after the transform)
+  T kv[KIDX ? 1 : 16];
+  unsigned kb[4];                                       // 16 byte indices, packed
+  if constexpr (Ops::KIN && KIDX) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      unsigned x = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        x |= (unsigned)__ldcs(I.kidx + base + Geo::off(bn, jn + ((4 * w + e) << (LOGL - 4)))) << (8 * e);
+      kb[w] = x;
+    }
+  } else if constexpr (Ops::KIN) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + base + Geo::off(bn, jn + (q << (LOGL - 4))));
+  }
+  if constexpr (Ops::FWD) G::dft(sm, tw_line, v);
+  if constexpr (Ops::COL_TW) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = twmul(v[q], __ldg(I.tw_col + outer * (jn + (q << (LB - 4)))));
+  }
+  if constexpr (Ops::BIG_TW) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      v[q] = twmul(v[q], big_twiddle<T, M1, M2>(I, c0 + bn, outer + ((jn + (q << (LA - 4))) << LB)));
+  }
+  if constexpr (Ops::KIN) {
+    if constexpr (KIDX) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kval<T, LUT_SMEM>(lut, (kb[q >> 2] >> (8 * (q & 3))) & 255u));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
+    }
+    G::idft(sm, tw_line, v);
+  }
+  if constexpr (Ops::SPEC) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const T x = cscale(v[q], I.inv_n);
+      size_t chi;
+      if constexpr (KIND == kR2BFwd) {
+        // bin (g + B e) n2 + xi2, g = outer, e = output index, xi2 = column
+        const int e = jn + (q << (LA - 4));
+        chi = ((size_t)(outer + (e << LB)) << M2) + c0 + bn;
+      } else {
+        // row r = e + A g of the rank-1 array; bin (g + B e) + N2 xi1, xi1 = output index
+        const int r = (t << Geo::LOGC) + bn;
+        const int e = r & ((1 << LA) - 1), g = r >> LA;
+        chi = (size_t)(g + (e << LB)) + ((size_t)(jn + (q << (LOGL - 4))) << M1);
+      }
+      I.spec[chi] = make_double2((double)x.x, (double)x.y);
+    }
+  } else if constexpr (Ops::NAT_OUT) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) stst(I.u + base + Geo::off(bn, jn + (q << (LOGL - 4))), v[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) stst(I.u + base + Geo::off(b, j + (r << (LOGL - LR1))), v[q * R1 + r]);
+    }
+  }
+}
+
+template <typename T, int M1, int M2, int KIND, bool KIDX = false>
+__global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MINB_2T : S4Cfg<T>::MINB)
+    sweep4(const __grid_constant__ S4Inst<T> I) {
+  using Geo = S4Geo<T, M1, M2, KIND>;
   extern __shared__ __align__(128) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  const T* tw_line = Geo::ROW ? I.tw_rows : Geo::SWEEP_A ? I.tw_b : I.tw_a;
   // K sweeps: K from a table of at most 256 values indexed by one byte per point
-  __shared__ T klut[Ops::KIN && KIDX ? 256 : 1];
-  if constexpr (Ops::KIN && KIDX) {
+  __shared__ T klut[S4Ops<KIND>::KIN && KIDX ? 256 : 1];
+  if constexpr (S4Ops<KIND>::KIN && KIDX) {
     for (int i = threadIdx.x; i < I.nlut; i += Geo::NT) klut[i] = I.klut[i];
     __syncthreads();
   }
+  for (int t = blockIdx.x; t < Geo::NTILES; t += gridDim.x) sweep4_tile<T, M1, M2, KIND, KIDX, true>(I, t, sm, klut);
+}
 
-  for (int t = blockIdx.x; t < Geo::NTILES; t += gridDim.x) {
-    int outer, c0;
-    const size_t base = Geo::base(t, outer, c0);
-    T v[16];
-    int bn, jn;                                          // this thread's natural-order line and butterfly
-    G::template bm<4>(0, bn, jn);
-    if constexpr (Ops::INV_IN) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = ldst(I.u + base + Geo::off(bn, jn + (q << (LOGL - 4))));
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) v[q * R1 + r] = ldst(I.u + base + Geo::off(b, j + (r << (LOGL - LR1))));
-      }
-    }
-    __syncthreads();                                     // previous tile's exchange reads done
+// Several instances of one array shape in one launch: tile t of the launch is local tile
+// map[t].y of instance map[t].x (each instance with its own state, tables and step size).
+template <typename T> struct S4Batch {
+  const S4Inst<T>* inst;
+  const int2* map;
+  int ntiles;
+};
 
-    // ---- inverse half: natural order in, pass-1 pattern out ----
-    if constexpr (Ops::CONJ_COL) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = twmulc(v[q], __ldg(I.tw_col + outer * (jn + (q << (LB - 4)))));
-    }
-    if constexpr (Ops::CONJ_BIG) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        v[q] = twmulc(v[q], big_twiddle<T, M1, M2>(I, c0 + bn, outer + ((jn + (q << (LA - 4))) << LB)));
-    }
-    if constexpr (Ops::INV_IN) G::idft(sm, tw_line, v);
-
-    // ---- physical samples: 1/n and the potential phase ----
-    if constexpr (Ops::HAS_P) {
-      const T* P = Ops::FULL_P ? I.Pf : I.Ph;
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) {
-          T x = v[q * R1 + r];
-          if constexpr (Ops::INV_IN) x = cscale(x, I.inv_n);
-          v[q * R1 + r] = apply_phase(x, ldtab(P + base + Geo::off(b, j + (r << (LOGL - LR1)))));
-        }
-      }
-    }
-
-    // ---- forward half: pass-1 pattern in, natural order out ----
-    // K is loaded before the transform so that its latency hides behind it (measured: a
-    // quarter of the four-sweep step's time at 2^22 when loaded after the transform)
-    T kv[KIDX ? 1 : 16];
-    unsigned kb[4];                                       // 16 byte indices, packed
-    if constexpr (Ops::KIN && KIDX) {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        unsigned x = 0;
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          x |= (unsigned)__ldcs(I.kidx + base + Geo::off(bn, jn + ((4 * w + t) << (LOGL - 4)))) << (8 * t);
-        kb[w] = x;
-      }
-    } else if constexpr (Ops::KIN) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + base + Geo::off(bn, jn + (q << (LOGL - 4))));
-    }
-    if constexpr (Ops::FWD) G::dft(sm, tw_line, v);
-    if constexpr (Ops::COL_TW) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = twmul(v[q], __ldg(I.tw_col + outer * (jn + (q << (LB - 4)))));
-    }
-    if constexpr (Ops::BIG_TW) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        v[q] = twmul(v[q], big_twiddle<T, M1, M2>(I, c0 + bn, outer + ((jn + (q << (LA - 4))) << LB)));
-    }
-    if constexpr (Ops::KIN) {
-      if constexpr (KIDX) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], klut[(kb[q >> 2] >> (8 * (q & 3))) & 255u]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
-      }
-      G::idft(sm, tw_line, v);
-    }
-    if constexpr (Ops::SPEC) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const T x = cscale(v[q], I.inv_n);
-        size_t chi;
-        if constexpr (KIND == kR2BFwd) {
-          // bin (g + B e) n2 + xi2, g = outer, e = output index, xi2 = column
-          const int e = jn + (q << (LA - 4));
-          chi = ((size_t)(outer + (e << LB)) << M2) + c0 + bn;
-        } else {
-          // row r = e + A g of the rank-1 array; bin (g + B e) + N2 xi1, xi1 = output index
-          const int r = (t << Geo::LOGC) + bn;
-          const int e = r & ((1 << LA) - 1), g = r >> LA;
-          chi = (size_t)(g + (e << LB)) + ((size_t)(jn + (q << (LOGL - 4))) << M1);
-        }
-        I.spec[chi] = make_double2((double)x.x, (double)x.y);
-      }
-    } else if constexpr (Ops::NAT_OUT) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) stst(I.u + base + Geo::off(bn, jn + (q << (LOGL - 4))), v[q]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16 / R1; ++q) {
-        int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) stst(I.u + base + Geo::off(b, j + (r << (LOGL - LR1))), v[q * R1 + r]);
-      }
-    }
+template <typename T, int M1, int M2, int KIND, bool KIDX = false>
+__global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MINB_2T : S4Cfg<T>::MINB)
+    sweep4_batch(const __grid_constant__ S4Batch<T> B) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+    const int2 m = B.map[t];
+    const S4Inst<T> I = B.inst[m.x];
+    sweep4_tile<T, M1, M2, KIND, KIDX, false>(I, m.y, sm, I.klut);
   }
 }
 
@@ -291,6 +321,8 @@ __global__ void __launch_bounds__(S4Cfg<T>::NT, S4Ops<KIND>::TWO ? S4Cfg<T>::MIN
 struct S4Kernels {
   const void* k[kS4Kinds] = {};
   const void* k_kidx = nullptr;   // the K sweep reading K through kidx
+  const void* b[kS4Kinds] = {};   // rank-1 shapes up to 2^22: the multi-instance (batch) kernels
+  const void* b_kidx = nullptr;
   int ntiles[3] = {};
 };
 
@@ -319,6 +351,15 @@ template <typename T, int M1, int M2, bool RANK1> S4Kernels s4_kernels() {
     K.k[kZ] = (const void*)sweep4<T, M1, M2, kZ>;
     K.k[kZFwd] = (const void*)sweep4<T, M1, M2, kZFwd>;
     K.k_kidx = (const void*)sweep4<T, M1, M2, kZ, true>;
+    if constexpr (M1 + M2 <= 22) {   // larger instances fill the GPU one at a time
+      K.b[kXHead] = (const void*)sweep4_batch<T, M1, M2, kXHead>;
+      K.b[kXMid] = (const void*)sweep4_batch<T, M1, M2, kXMid>;
+      K.b[kXTail] = (const void*)sweep4_batch<T, M1, M2, kXTail>;
+      K.b[kY] = (const void*)sweep4_batch<T, M1, M2, kY>;
+      K.b[kYInv] = (const void*)sweep4_batch<T, M1, M2, kYInv>;
+      K.b[kZ] = (const void*)sweep4_batch<T, M1, M2, kZ>;
+      K.b_kidx = (const void*)sweep4_batch<T, M1, M2, kZ, true>;
+    }
     K.ntiles[0] = S4Geo<T, M1, M2, kZ>::NTILES;
     K.ntiles[1] = S4Geo<T, M1, M2, kXMid>::NTILES;
     K.ntiles[2] = S4Geo<T, M1, M2, kY>::NTILES;

@@ -31,7 +31,8 @@ bool s4_supports_rank1(int prec, int m) {
 }
 
 template <typename T> static S4Inst<T> s4_inst(lsp_plan p, void* state) {
-  S4Inst<T> I{};
+  S4Inst<T> I;
+  memset(&I, 0, sizeof(I));   // padding too: descriptors are compared bytewise
   I.u = (T*)state;
   I.Ph = (const T*)p->Ph;
   I.Pf = (const T*)p->Pf;
@@ -159,6 +160,97 @@ template <typename T> static int s4_spectral_impl(lsp_plan p, cudaStream_t s) {
     if (!rc) rc = s4_launch<T>(K.k[kZFwd], I, K.ntiles[0], s);
   }
   return rc;
+}
+
+// --------------------------------------------------------------------------
+// Batches: all instances of one rank-1 size in each sweep's launch
+// --------------------------------------------------------------------------
+bool s4_batchable(lsp_plan p) {
+  S4Kernels K;
+  return p->path == kPathRank1x4 && s4_lookup(p, &K) && K.b[kXHead] != nullptr;
+}
+
+int s4_class_init(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans) {
+  S4Kernels K;
+  if (c.ids.empty() || !s4_lookup(plans[c.ids[0]], &K)) return LSP_ERR_UNSUPPORTED;
+  for (int g = 0; g < 3; ++g) {
+    std::vector<int2> map;
+    for (size_t k = 0; k < c.ids.size(); ++k)
+      for (int t = 0; t < K.ntiles[g]; ++t) map.push_back(make_int2((int)k, t));
+    c.total[g] = (int)map.size();
+    if (cudaMalloc(&c.map[g], map.size() * sizeof(int2)) != cudaSuccess) return LSP_ERR_OOM;
+    LSP_CUDA_TRY(cudaMemcpy(c.map[g], map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  // kernel attributes and grid sizes are set and cached here, outside any graph capture
+  static_assert(S4Cfg<float2>::NT == S4Cfg<double2>::NT && S4Cfg<float2>::TILE == S4Cfg<double2>::TILE, "");
+  const size_t smem = (size_t)S4Cfg<float2>::TILE * (plans[c.ids[0]]->prec == LSP_C64 ? 8 : 16);
+  int grid = 0, rc = LSP_OK;
+  for (const void* fn : K.b)
+    if (fn && (rc = s4_grid(fn, S4Cfg<float2>::NT, smem, &grid))) return rc;
+  if (K.b_kidx && (rc = s4_grid(K.b_kidx, S4Cfg<float2>::NT, smem, &grid))) return rc;
+  return LSP_OK;
+}
+
+template <typename T>
+static int s4_class_sync_impl(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed) {
+  std::vector<unsigned char> h(c.ids.size() * sizeof(S4Inst<T>));
+  for (size_t k = 0; k < c.ids.size(); ++k) {
+    lsp_plan p = plans[c.ids[k]];
+    if ((p->kidx != nullptr) != c.kidx) return LSP_ERR_BAD_ARG;   // K form changed since creation
+    const S4Inst<T> I = s4_inst<T>(p, p->u);
+    memcpy(h.data() + k * sizeof(I), &I, sizeof(I));
+  }
+  *changed = h != c.inst_host;
+  if (!*changed) return LSP_OK;
+  if (!c.inst && cudaMalloc(&c.inst, h.size()) != cudaSuccess) return LSP_ERR_OOM;
+  LSP_CUDA_TRY(cudaMemcpy(c.inst, h.data(), h.size(), cudaMemcpyHostToDevice));
+  c.inst_host = h;
+  return LSP_OK;
+}
+
+int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed) {
+  const int prec = plans[c.ids[0]]->prec;
+  return prec == LSP_C64 ? s4_class_sync_impl<float2>(c, plans, changed)
+                         : s4_class_sync_impl<double2>(c, plans, changed);
+}
+
+template <typename T> static int s4b_launch(const void* fn, const lsp_batch_s::S4Class& c, int g, cudaStream_t s) {
+  constexpr int NT = S4Cfg<T>::NT;
+  constexpr size_t smem = (size_t)S4Cfg<T>::TILE * sizeof(T);
+  int grid = 0;
+  int rc = s4_grid(fn, NT, smem, &grid);
+  if (rc) return rc;
+  grid = std::max(1, std::min(c.total[g], grid));
+  S4Batch<T> B{(const S4Inst<T>*)c.inst, c.map[g], c.total[g]};
+  void* args[] = {(void*)&B};
+  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s));
+  return LSP_OK;
+}
+
+// The same sweep order as one instance's steps (s4_launch_steps), over all instances.
+template <typename T> static int s4_class_steps_impl(const lsp_batch_s::S4Class& c, int64_t nsteps, cudaStream_t s) {
+  S4Kernels K;
+  if (!s4_kernels_rank1(sizeof(T) == 8 ? LSP_C64 : LSP_C128, c.m, &K) || !K.b[kXHead]) return LSP_ERR_UNSUPPORTED;
+  const void* kin = c.kidx ? K.b_kidx : K.b[kZ];
+  int rc = LSP_OK;
+  for (int64_t st = 0; st < nsteps && !rc; ++st) {
+    rc = s4b_launch<T>(K.b[st == 0 ? kXHead : kXMid], c, 1, s);
+    if (!rc) rc = s4b_launch<T>(K.b[kY], c, 2, s);
+    if (!rc) rc = s4b_launch<T>(kin, c, 0, s);
+    if (!rc) rc = s4b_launch<T>(K.b[kYInv], c, 2, s);
+  }
+  if (!rc) rc = s4b_launch<T>(K.b[kXTail], c, 1, s);
+  return rc;
+}
+
+int s4_class_steps(const lsp_batch_s::S4Class& c, int prec, int64_t nsteps, cudaStream_t s) {
+  return prec == LSP_C64 ? s4_class_steps_impl<float2>(c, nsteps, s) : s4_class_steps_impl<double2>(c, nsteps, s);
+}
+
+void s4_class_free(lsp_batch_s::S4Class& c) {
+  cudaFree(c.inst);
+  for (int g = 0; g < 3; ++g) cudaFree(c.map[g]);
+  c.inst = nullptr;
 }
 
 int s4_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {

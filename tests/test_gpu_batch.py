@@ -74,3 +74,43 @@ def test_batch_rejects_mixed_precision(lib):
     with pytest.raises(lib.LspError) as e:
         lib.Batch([a, b])
     assert e.value.code == -8
+
+
+def test_batch_of_four_sweep_instances(lib):
+    """Rank-1 four-sweep instances of 2^20 points (d = 3..8, each with its own z, v and dt;
+    K read from the table or through the byte index, two groups) advance together, one launch
+    per sweep, beside a two-sweep and an SMEM-resident instance.  A 20-step call replays a
+    captured graph, a 5-step call launches directly; each instance ends where it ends when
+    stepped alone, and two of them are checked against the oracle."""
+    import torch
+    pool = w.c3()
+    big = [i for i in pool if i.npoints == 1 << 20]
+    ds = sorted({i.d for i in big})
+    four = [next(i for i in big if i.d == d) for d in (ds[0], ds[-1])] + [i for i in big if i.d not in (ds[0], ds[-1])][:2]
+    others = [next(i for i in pool if i.npoints == 1 << 16), next(i for i in pool if i.npoints == 1 << 12)]
+    insts = four + others
+    plans, ref_in = _setup(lib, insts, "c64")
+    singles, _ = _setup(lib, insts, "c64")
+    for p, q in zip(plans[:4], singles[:4]):
+        p.set_path(lib.PATH_RANK1_4SWEEP)
+        q.set_path(lib.PATH_RANK1_4SWEEP)
+    kidx = [p.info()["max_norm2"] < 256 for p in plans[:4]]
+    assert any(kidx) and not all(kidx), kidx                  # both K forms
+    batch = lib.Batch(plans)
+    dts = [inst.dt for inst in insts]
+    for n in (20, 5, 20):
+        batch.steps(dts, n)
+        for q, dt in zip(singles, dts):
+            q.strang_steps(dt, n)
+    assert batch.status() == 0
+    for k, (p, q, inst) in enumerate(zip(plans, singles, insts)):
+        g = p.get_state(prec="c128").cpu().numpy()
+        s = q.get_state(prec="c128").cpu().numpy()
+        assert np.linalg.norm(g - s) / np.linalg.norm(s) < 1e-6, inst.name
+    for k in (0, 1):
+        inst, (v, u0) = insts[k], ref_in[k]
+        norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+        ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 45)
+        g = plans[k].get_state(prec="c128").cpu().numpy()
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < TOL["c64"], inst.name
+    batch.destroy()
