@@ -87,8 +87,8 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
- * 0, 3, 1; rank 2: 1, 2; reported by lsp_plan_info, changed by
- * lsp_plan_set_path or lsp_plan_autotune):
+ * 0, 3, 1, but 3, 0, 1 for complex64 with n >= 2^20; rank 2: 1, 2; reported
+ * by lsp_plan_info, changed by lsp_plan_set_path or lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
  *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, rank 1 or 2;
  *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of

@@ -595,10 +595,11 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   DeviceGuard guard(device);
   const size_t sz = csize(prec);
   // ---- choose the path: rank-1 two-sweep, rank-1 four-sweep, SMEM-resident; rank-2 SMEM, four-sweep ----
-  // complex64 from 2^22 points on: the four-sweep path measured 11-19 % faster than the
-  // two-sweep kernel (50.0 against 45.1 G point-steps/s at 2^22, 53.8 against 45.1 at 2^23)
+  // complex64 from 2^20 points on: the four-sweep path measured faster than the two-sweep
+  // kernel (G point-steps/s: 44.7 against 43.6 at 2^20, 50.0 against 45.1 at 2^22, 53.8
+  // against 45.1 at 2^23; 32 batched instances of 2^20: 58.6 against 49.8)
   const int logn0 = ilog2exact(ntot);
-  const bool four_first = prec == LSP_C64 && logn0 >= 22;
+  const bool four_first = prec == LSP_C64 && logn0 >= 20;
   const int order1[] = {four_first ? kPathRank1x4 : kPathMultipass, four_first ? kPathMultipass : kPathRank1x4,
                         kPathSmall};
   const int order2[] = {kPathSmall, kPathRank2};

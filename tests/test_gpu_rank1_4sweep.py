@@ -86,7 +86,8 @@ def test_four_sweep_spectral(lib):
 def test_paths_set_path_and_errors(lib):
     inst = w.c2(20)
     plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64")
-    assert plan.info()["path"] == lib.PATH_MULTIPASS
+    assert plan.info()["path"] == lib.PATH_RANK1_4SWEEP         # complex64 default from 2^20
+    assert lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128").info()["path"] == lib.PATH_MULTIPASS
     assert set(plan.paths()) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP}
     with pytest.raises(lib.LspError) as e:
         plan.set_path(lib.PATH_RANK2)
