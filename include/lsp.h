@@ -87,10 +87,13 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
- * 0, 3, 1, but 3, 0, 1 for complex64 with n >= 2^20; rank 2: 1, 2; reported
- * by lsp_plan_info, changed by lsp_plan_set_path or lsp_plan_autotune):
+ * 0, 3, 1, but for complex64 1, 3, 0 at n = 2^13 and 3, 0, 1 from n = 2^20;
+ * rank 2: 1, 2; reported by lsp_plan_info, changed by lsp_plan_set_path or
+ * lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
- *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, rank 1 or 2;
+ *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, rank 1 or 2
+ *     (rank 1 with n = 2^11 .. 2^13 (complex64) or 2^11 .. 2^12 (complex128): the
+ *     state stays in registers across the steps, one line FFT per step);
  *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
  *     (10, 8), (11, 9), (12, 10), (14, 12);
  *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25}.

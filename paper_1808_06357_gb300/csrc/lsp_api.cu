@@ -508,6 +508,12 @@ static int setup_path_tables(lsp_plan p, int path) {
     for (int i = 0; i < p->naxes; ++i) twid(tw, p->axes[i].len, p->axes[i].len, true);
   }
   if ((rc = upload(p, &p->tw_small, tw))) return rc;
+  if (logn > 0 && small_line_supported(prec, p->r, logn)) {
+    // power-of-two rank-1 lattice: per-pass tables of the one-line kernel
+    tw.clear();
+    passes(tw, logn);
+    if ((rc = upload(p, &p->tw_pass, tw))) return rc;
+  }
   p->N1 = (int)p->n[p->r - 1];
   p->N2 = p->r == 2 ? (int)p->n[0] : 1;
   return small_upload_desc(p, 0);
@@ -598,10 +604,13 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   // complex64 from 2^20 points on: the four-sweep path measured faster than the two-sweep
   // kernel (G point-steps/s: 44.7 against 43.6 at 2^20, 50.0 against 45.1 at 2^22, 53.8
   // against 45.1 at 2^23; 32 batched instances of 2^20: 58.6 against 49.8)
+  // complex64 at 2^13 points: the SMEM-resident line kernel (15 batched instances, 500
+  // steps: 4.6 ms against 8.4 ms for the two-sweep kernel)
   const int logn0 = ilog2exact(ntot);
   const bool four_first = prec == LSP_C64 && logn0 >= 20;
-  const int order1[] = {four_first ? kPathRank1x4 : kPathMultipass, four_first ? kPathMultipass : kPathRank1x4,
-                        kPathSmall};
+  const bool small_first = prec == LSP_C64 && r == 1 && logn0 == 13;
+  const int order1[] = {small_first ? kPathSmall : four_first ? kPathRank1x4 : kPathMultipass,
+                        four_first ? kPathMultipass : kPathRank1x4, small_first ? kPathMultipass : kPathSmall};
   const int order2[] = {kPathSmall, kPathRank2};
   int path = -1;
   if (r == 1) {

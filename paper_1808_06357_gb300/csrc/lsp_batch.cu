@@ -1,6 +1,7 @@
 // Batched Strang stepping: many independent instances (uneven n, d and dt)
 // advanced together.  Instances are grouped once at creation:
-//  * SMEM-resident instances: one launch, one CTA per instance, all steps;
+//  * SMEM-resident instances: one CTA per instance running all steps; one launch
+//    per power-of-two size with the line kernel, one for all the others;
 //  * multipass instances: one group per lattice size 2^m (kernels are
 //    specialised per size); each group is a head sweep, one persistent
 //    cooperative launch over the tiles of all its instances, and a tail sweep;
@@ -31,7 +32,7 @@ struct DeviceGuard {
 
 void free_batch(lsp_batch b) {
   if (!b) return;
-  cudaFree(b->small_desc);
+  for (auto& g : b->smalls) cudaFree(g.desc);
   for (auto& c : b->classes) {
     cudaFree(c.desc);
     cudaFree(c.colmap);
@@ -107,13 +108,13 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   DeviceGuard g(dev);
   auto fail = [&](int code) { free_batch(b); return code; };
 
-  std::map<int, std::vector<int>> by_m;
+  std::map<int, std::vector<int>> by_m, by_line;
   std::map<std::pair<int, bool>, std::vector<int>> by_m4;
   for (int i = 0; i < count; ++i) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
     else if (s4_batchable(plans[i])) by_m4[{plans[i]->logn, plans[i]->kidx != nullptr}].push_back(i);
     else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4) b->seq_ids.push_back(i);
-    else b->small_ids.push_back(i);
+    else by_line[small_line_logn(plans[i])].push_back(i);
   }
   for (auto& kv : by_m4) {
     b->s4classes.emplace_back();
@@ -126,17 +127,21 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
     if (!rc) rc = s4_class_sync(c, b->plans, &changed);
     if (rc) return fail(rc);
   }
-  // SMEM-resident group
-  if (!b->small_ids.empty()) {
+  // SMEM-resident groups
+  for (auto& kv : by_line) {
+    b->smalls.emplace_back();
+    lsp_batch_s::SmallGroup& sg = b->smalls.back();
+    sg.line_logn = kv.first;
+    sg.ids = kv.second;
     const size_t ds = (size_t)small_desc_size(prec);
-    std::vector<unsigned char> host(ds * b->small_ids.size());
-    for (size_t k = 0; k < b->small_ids.size(); ++k) {
-      lsp_plan p = plans[b->small_ids[k]];
+    std::vector<unsigned char> host(ds * sg.ids.size());
+    for (size_t k = 0; k < sg.ids.size(); ++k) {
+      lsp_plan p = plans[sg.ids[k]];
       small_fill_desc(p, host.data() + k * ds);
-      b->small_max_n = std::max(b->small_max_n, (int)p->ntot);
+      sg.max_n = std::max(sg.max_n, (int)p->ntot);
     }
-    if (cudaMalloc(&b->small_desc, host.size()) != cudaSuccess) return fail(LSP_ERR_OOM);
-    if (cudaMemcpy(b->small_desc, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMalloc(&sg.desc, host.size()) != cudaSuccess) return fail(LSP_ERR_OOM);
+    if (cudaMemcpy(sg.desc, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(LSP_ERR_CUDA);
   }
   // one class per lattice size
@@ -185,8 +190,8 @@ int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream)
     int rc = build_phase_tables(b->plans[i], dt[i], s);
     if (rc) return rc;
   }
-  if (!b->small_ids.empty()) {
-    int rc = small_batch_launch(b->prec, b->small_desc, (int)b->small_ids.size(), b->small_max_n, nsteps, s);
+  for (auto& sg : b->smalls) {
+    int rc = small_batch_launch(b->prec, sg.desc, (int)sg.ids.size(), sg.max_n, sg.line_logn, nsteps, s);
     if (rc) return rc;
   }
   if (!b->s4classes.empty()) {

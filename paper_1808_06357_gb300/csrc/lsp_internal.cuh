@@ -114,10 +114,15 @@ struct lsp_batch_s {
   std::vector<int> seq_ids;      // four-sweep instances, stepped one after another
   std::vector<int> paths;        // each plan's execution path when the batch was made
   int device = 0;
-  // SMEM-resident instances: one CTA each, one launch for all of them
-  std::vector<int> small_ids;
-  void* small_desc = nullptr;    // device array of their kernel descriptors
-  int small_max_n = 0;
+  // SMEM-resident instances: one CTA each, one launch per group (the line kernel's
+  // instances by size, line_logn = log2 n; all others together, line_logn = 0)
+  struct SmallGroup {
+    int line_logn = 0;
+    std::vector<int> ids;
+    void* desc = nullptr;        // device array of their kernel descriptors
+    int max_n = 0;
+  };
+  std::vector<SmallGroup> smalls;
   // multipass instances grouped by lattice size 2^m (one kernel per size)
   struct Class {
     int m = 0;
@@ -298,7 +303,11 @@ int small_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 // batching hooks: descriptor bytes of a plan, and launches over descriptor arrays
 int small_desc_size(int prec);
 void small_fill_desc(lsp_plan p, void* host_out);
-int small_batch_launch(int prec, const void* ddesc, int count, int max_n, int64_t nsteps, cudaStream_t s);
+// line_logn > 0: all `count` instances are rank 1 with n = 2^line_logn and run the line kernel
+int small_batch_launch(int prec, const void* ddesc, int count, int max_n, int line_logn, int64_t nsteps,
+                       cudaStream_t s);
+bool small_line_supported(int prec, int r, int logn);   // rank 1, n = 2^logn: line kernel exists
+int small_line_logn(lsp_plan p);                        // log2 n if the plan runs the line kernel, else 0
 int multipass_desc_size(int prec);
 void multipass_fill_desc(lsp_plan p, void* host_out, int* ncol, int* nrow);
 int multipass_batch_steps(int prec, int m, const void* ddesc, const int2* colmap, const int2* rowmap, int ninst,

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "lsp_internal.cuh"
+#include "lsp_tile.cuh"
 
 namespace lsp {
 
@@ -31,6 +32,8 @@ template <typename T> struct SmallDesc {
   SmallAxis axes[2];
   R inv_n;           // 1/n rounded
   R inv_n_lo;        // 1/n - inv_n
+  const T* twl;      // rank 1, n = 2^logn with a line kernel: its per-pass twiddles (else null)
+  int logn;
 };
 
 template <int DIR, typename T>
@@ -134,6 +137,83 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const SmallDesc<T>
   for (int k = threadIdx.x; k < n; k += blockDim.x) S.u[k] = cur[k];
 }
 
+// --------------------------------------------------------------------------
+// Rank 1, n = 2^m (2^11 .. 2^13): the whole lattice is one line of the tile FFT
+// (16 points per thread, NT = n / 16 threads), held in registers across all
+// steps; shared memory only carries the exchanges between radix-16 passes.
+// Per step: forward line DFT (natural bin order out), K by bin, inverse line DFT
+// (back to the load pattern), 1/n (exact) and the potential phase.
+// --------------------------------------------------------------------------
+template <typename T> constexpr bool small_line_ok(int logn) {
+  return logn >= 11 && logn <= (sizeof(T) == 8 ? 13 : 12);
+}
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4)) small_line_kernel(const SmallDesc<T>* D, long long nsteps) {
+  constexpr int NT = 1 << (LOGN - 4);
+  using G = Line<T, NT, LOGN, true>;
+  constexpr int LR1 = G::LOGR1, R1 = G::R1;
+  const SmallDesc<T>& S = D[blockIdx.x];
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  if (nsteps <= 0) return;
+  const T* __restrict__ tw = S.twl;
+  // element index of register q*R1+r in the load pattern, and of register q in natural order
+  auto in_at = [](int q, int r) { int b, j; G::template bm<LR1>(q, b, j); return j + (r << (LOGN - LR1)); };
+  int bn, jn;
+  G::template bm<4>(0, bn, jn);
+  T v[16];
+#pragma unroll
+  for (int q = 0; q < 16 / R1; ++q)
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = in_at(q, r);
+      v[q * R1 + r] = apply_phase(S.u[i], __ldg(S.Ph + i));
+    }
+  const auto inv_n = S.inv_n;                         // exact: n is a power of two
+  for (long long step = 0; step < nsteps; ++step) {
+    T kv[16], pv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) kv[q] = __ldg(S.K + jn + (q << (LOGN - 4)));
+    G::dft(sm, tw, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
+    const T* P = step + 1 < nsteps ? S.Pf : S.Ph;
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) pv[q * R1 + r] = __ldg(P + in_at(q, r));
+    G::idft(sm, tw, v);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = apply_phase(cscale(v[k], inv_n), pv[k]);
+  }
+#pragma unroll
+  for (int q = 0; q < 16 / R1; ++q)
+#pragma unroll
+    for (int r = 0; r < R1; ++r) S.u[in_at(q, r)] = v[q * R1 + r];
+}
+
+template <typename T> static int small_line_launch(const void* desc, int count, int logn, long long nsteps, cudaStream_t s) {
+  const void* fn = nullptr;
+  switch (logn) {
+    case 11: fn = (const void*)small_line_kernel<T, 11>; break;
+    case 12: fn = (const void*)small_line_kernel<T, 12>; break;
+    case 13: if constexpr (small_line_ok<T>(13)) fn = (const void*)small_line_kernel<T, 13>; break;
+    default: break;
+  }
+  if (!fn) return LSP_ERR_UNSUPPORTED;
+  const size_t smem = ((size_t)1 << logn) * sizeof(T);
+  LSP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const void* d = desc;
+  void* args[] = {(void*)&d, (void*)&nsteps};
+  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(count), dim3(1u << (logn - 4)), args, smem, s));
+  return LSP_OK;
+}
+
+bool small_line_supported(int prec, int r, int logn) {
+  return r == 1 && (prec == LSP_C64 ? small_line_ok<float2>(logn) : small_line_ok<double2>(logn));
+}
+
 template <typename T> static SmallDesc<T> make_small(lsp_plan p) {
   SmallDesc<T> S{};
   S.u = (T*)p->u;
@@ -149,6 +229,8 @@ template <typename T> static SmallDesc<T> make_small(lsp_plan p) {
   S.axes[1] = p->axes[1];
   S.inv_n = (decltype(S.inv_n))(1.0 / (double)p->ntot);
   S.inv_n_lo = (decltype(S.inv_n))(1.0 / (double)p->ntot - (double)S.inv_n);
+  S.twl = (const T*)p->tw_pass;
+  S.logn = p->tw_pass ? p->logn : 0;
   return S;
 }
 
@@ -174,9 +256,18 @@ static int small_launch(const void* desc, int count, int max_n, long long nsteps
   return cuda_status(cudaGetLastError());
 }
 
+// Steps of `count` instances from a descriptor array: the line kernel when line_logn > 0
+// (every instance of that size), else the mixed-radix kernel.
+template <typename T>
+static int small_steps_launch(const void* desc, int count, int max_n, int line_logn, long long nsteps, cudaStream_t s) {
+  if (line_logn > 0) return small_line_launch<T>(desc, count, line_logn, nsteps, s);
+  return small_launch<T>(desc, count, max_n, nsteps, 0, s);
+}
+
 int small_steps(lsp_plan p, int64_t nsteps, cudaStream_t s) {
-  return p->prec == LSP_C64 ? small_launch<float2>(p->desc, 1, (int)p->ntot, nsteps, 0, s)
-                            : small_launch<double2>(p->desc, 1, (int)p->ntot, nsteps, 0, s);
+  const int ll = p->tw_pass ? p->logn : 0;
+  return p->prec == LSP_C64 ? small_steps_launch<float2>(p->desc, 1, (int)p->ntot, ll, nsteps, s)
+                            : small_steps_launch<double2>(p->desc, 1, (int)p->ntot, ll, nsteps, s);
 }
 
 int small_spectral(lsp_plan p, cudaStream_t s) {
@@ -191,7 +282,7 @@ template <typename T> static int small_steps_on_impl(lsp_plan p, void* state, in
   S.u = (T*)state;
   SmallDesc<T>* d = (SmallDesc<T>*)p->desc + 1;
   LSP_CUDA_TRY(cudaMemcpyAsync(d, &S, sizeof(S), cudaMemcpyHostToDevice, s));
-  return small_launch<T>(d, 1, (int)p->ntot, nsteps, 0, s);
+  return small_steps_launch<T>(d, 1, (int)p->ntot, S.logn, nsteps, s);
 }
 
 int small_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
@@ -212,9 +303,12 @@ void small_fill_desc(lsp_plan p, void* host_out) {
   }
 }
 
-int small_batch_launch(int prec, const void* ddesc, int count, int max_n, int64_t nsteps, cudaStream_t s) {
-  return prec == LSP_C64 ? small_launch<float2>(ddesc, count, max_n, nsteps, 0, s)
-                         : small_launch<double2>(ddesc, count, max_n, nsteps, 0, s);
+int small_line_logn(lsp_plan p) { return p->tw_pass ? p->logn : 0; }
+
+int small_batch_launch(int prec, const void* ddesc, int count, int max_n, int line_logn, int64_t nsteps,
+                       cudaStream_t s) {
+  return prec == LSP_C64 ? small_steps_launch<float2>(ddesc, count, max_n, line_logn, nsteps, s)
+                         : small_steps_launch<double2>(ddesc, count, max_n, line_logn, nsteps, s);
 }
 
 }  // namespace lsp

@@ -114,3 +114,35 @@ def test_batch_of_four_sweep_instances(lib):
         g = plans[k].get_state(prec="c128").cpu().numpy()
         assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < TOL["c64"], inst.name
     batch.destroy()
+
+
+@pytest.mark.parametrize("m,prec", [(11, "c64"), (12, "c64"), (13, "c64"), (11, "c128"), (12, "c128")])
+def test_small_line_kernel_parity(lib, m, prec):
+    """Rank-1 lattices of 2^11 .. 2^13 points run the SMEM-resident one-line kernel (state in
+    registers across steps): 40 steps against the oracle, alone and in a batch beside a
+    mixed-radix SMEM instance (n = 961) of the same call."""
+    inst = w.Instance(f"line 2^{m}", 5, (1 << m,), w.random_rank1(5, 1 << m, w.Rng(m, 9)), 0.1, 2e-3, 40,
+                      w.v_smooth, lambda p: w.gaussian_packet(p, 0.1, [0.5] * 5))
+    other = w.Instance("n=961", 2, (961,), np.array([1, 31]), 0.1, 1e-3, 40, w.v_smooth,
+                       lambda p: w.gaussian_packet(p, 0.1, [0.5] * 2))
+    plans, ref_in = _setup(lib, [inst, other], prec)
+    single, _ = _setup(lib, [inst], prec)
+    for p in (plans[0], single[0]):
+        if m >= 13:                                # two-sweep by default from 2^13
+            p.set_path(lib.PATH_SMALL)
+        assert p.info()["path"] == lib.PATH_SMALL
+    single[0].strang_steps(inst.dt, 25)
+    single[0].strang_steps(inst.dt, 15)
+    batch = lib.Batch(plans)
+    batch.steps([inst.dt, other.dt], 25)
+    batch.steps([inst.dt, other.dt], 15)
+    assert batch.status() == 0 and single[0].status() == 0
+    for k, it in enumerate((inst, other)):
+        v, u0 = ref_in[k]
+        norms, _ = L.minl2_norms_dp(it.Z, it.n)
+        ref = S.strang(u0, v, norms, it.n, it.gamma, it.dt, 40)
+        g = plans[k].get_state(prec="c128").cpu().numpy()
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < TOL[prec], it.name
+    s = single[0].get_state(prec="c128").cpu().numpy()
+    assert np.array_equal(s, plans[0].get_state(prec="c128").cpu().numpy())
+    batch.destroy()

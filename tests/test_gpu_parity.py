@@ -32,7 +32,7 @@ def host_state(plan):
     return plan.get_state(prec="c128").cpu().numpy()
 
 
-def run_both(lib, inst, prec, nsteps, aa="minl2", dt=None):
+def run_both(lib, inst, prec, nsteps, aa="minl2", dt=None, path=None):
     import torch
     dt = inst.dt if dt is None else dt
     P = L.lattice_points(inst.Z, inst.n)
@@ -42,6 +42,8 @@ def run_both(lib, inst, prec, nsteps, aa="minl2", dt=None):
         norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
     v, u0 = inst.v(P), inst.u0(P)
     plan = make_plan(lib, inst, prec, aa)
+    if path is not None:
+        plan.set_path(path)
     plan.set_potential(torch.from_numpy(v).cuda())
     plan.set_state(torch.from_numpy(u0).cuda())
     plan.strang_steps(dt, nsteps)
@@ -56,7 +58,7 @@ def run_both(lib, inst, prec, nsteps, aa="minl2", dt=None):
 # ---------------------------------------------------------------------------
 PLAN_CASES = [
     (w.c1(), "small"),
-    (w.c2(13), "multipass"),
+    (w.c2(13), "small"),
     (w.c2(16), "multipass"),
     (w.Instance("rank2", 3, (12, 6), np.array([[1, 0], [3, 1], [5, 5]]), 0.1, 1e-3, 10,
                 w.v_smooth, lambda p: w.gaussian_packet(p, 0.2, [0.5] * 3)), "small"),
@@ -137,7 +139,8 @@ def test_c1_full_run(lib, prec):
 def test_multipass_parity(lib, m, prec):
     inst = w.c2(m)
     nsteps = 50
-    got, ref, u0, _ = run_both(lib, inst, prec, nsteps)
+    got, ref, u0, plan = run_both(lib, inst, prec, nsteps, path=lib.PATH_MULTIPASS)
+    assert plan.info()["path"] == lib.PATH_MULTIPASS
     assert rel_l2(got, ref) < TOL[prec]
 
 
