@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 side measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plan", action="store_true", help="skip the plan-time (DP, CBC) side measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--no-rank2", action="store_true", help="skip the rank-2 2^14 x 2^12 batch measurement")
     ap.add_argument("--log2n", type=int, default=22, help="lattice size 2^m of the d=6 workload (profiling)")
@@ -392,11 +393,17 @@ def run_ours(args):
     if not args.no_rank2:
         rank2 = measure_rank2(args, lsp, torch, dev, local, flush, stream, world)
 
+    plan_time = None
+    if rank == 0 and not args.no_plan:
+        plan_time = measure_plan_time(lsp, inst, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, steps, el = cpu_oracle_rate(inst)
         cpu = {"value": rate, "unit": "lattice-point steps/s", "cores": 1, "kind": "oracle",
                "sample": f"{steps} FP64 Strang steps of the full n=2^22 state ({el:.1f} s, numpy FFT, 1 thread)"}
+        if plan_time is not None:
+            cpu["plan_time"] = cbc_oracle_time(plan_time)
 
     if rank == 0:
         out = {
@@ -418,6 +425,7 @@ def run_ours(args):
             "complex128": c128,
             "batched": batched,
             "rank2": rank2,
+            "plan_time": plan_time,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
@@ -428,6 +436,44 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_plan_time(lsp, inst, local):
+    """Plan-time work on the GPU: plan creation (minimal-l2 norms by the min-plus DP, tables) and the
+    component-by-component reconstructing lattice for C2's index set (HC(64), d=6, n=2^22, 400 seeded
+    candidates per component); the oracle's search on the same candidates is timed in the CPU-baseline leg."""
+    import workloads as w
+    t0 = time.perf_counter()
+    p = lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64", device=local)
+    t_plan = time.perf_counter() - t0
+    p.destroy()
+    I = w.hyperbolic_cross(6, 64)
+    n = 1 << 22
+    cand = w.cbc_candidates(6, n, 400, w.Rng(0, 21))
+    lsp.cbc_reconstructing(I, n, cand, device=local)           # warm-up (context, module load)
+    t0 = time.perf_counter()
+    Zg, fixed = lsp.cbc_reconstructing(I, n, cand, device=local)
+    t_gpu = time.perf_counter() - t0
+    out = {"plan_create_ms": 1e3 * t_plan,
+           "cbc": {"workload": "reconstructing rank-1 lattice for HC(64), d=6 (51,233 vectors), n=2^22, "
+                               "400 seeded candidates per component",
+                   "gpu_ms": 1e3 * t_gpu, "components_fixed": fixed, "z": [int(x) for x in Zg[:, 0]]}}
+    return out
+
+
+def cbc_oracle_time(plan_time):
+    """CPU-baseline leg of the plan-time measurement: the oracle's component-by-component search on
+    the same index set and candidates, timed on one host core."""
+    import workloads as w
+    from oracle import lattice as L
+    I = w.hyperbolic_cross(6, 64)
+    cand = w.cbc_candidates(6, 1 << 22, 400, w.Rng(0, 21))
+    t0 = time.perf_counter()
+    Zo, fo = L.cbc_reconstructing(I, 1 << 22, cand)
+    el = time.perf_counter() - t0
+    same = plan_time is not None and fo == plan_time["cbc"]["components_fixed"] and \
+        [int(x) for x in Zo[:, 0]] == plan_time["cbc"]["z"]
+    return {"cbc_oracle_ms": 1e3 * el, "cbc_same_lattice": bool(same)}
 
 
 def measure_batched(args, lsp, torch, dev, local, flush, stream, world, rank=0):

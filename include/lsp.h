@@ -298,6 +298,33 @@ int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double*
 int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, double dt, int64_t nsteps,
                              const double* v, const int32_t* norm2, void* u, void* stream);
 
+/*
+ * lsp_cbc_reconstructing -- a lattice on which h -> bin is injective on a given
+ * index set, built component by component on the GPU (Sec. 3.1 builds the
+ * paper's lattices by a component-by-component search; the acceptance test here
+ * is the injectivity that Def. 2 and Thm 1(iii) ask of the anti-aliasing set).
+ * Component 0 is fixed: z_0 = 1 (rank 1) or (z_{1,0}, z_{2,0}) = (1, 0) (rank 2,
+ * so that (1, 0) and (0, 1) are bins and the map onto Z_n1 x Z_n2 is onto).
+ * For j = 1 .. d-1 the first candidate of component j's list for which
+ *   h -> (h_0..h_j).(z_0..z_j) mod n            (rank 1), or
+ *   h -> ((h_0..h_j).(z_1..) mod n1) n2 + ((h_0..h_j).(z_2..) mod n2)  (rank 2)
+ * is injective on the projection of I onto its first j + 1 coordinates is kept.
+ *   I       m x d int32 (host), row-major: the index set (rows may repeat).
+ *   r       1 or 2;  n  r moduli (host), with n_1 (n_2) <= 2^31 and the bin
+ *           count n (rank 1) or n_1 n_2 (rank 2) <= 2^31.
+ *   cand    (d - 1) x ncand x r int64 (host): component j's candidates at
+ *           cand[((j - 1) ncand + t) r .. + r), tried in order t = 0, 1, ...
+ *   Z_out   d x r int64 (host), row-major: the components accepted (zeros after
+ *           the first component without an injective candidate).
+ *   fixed   (host, may be NULL) number of components fixed, d on success.
+ *   device  CUDA device ordinal.  Synchronous; holds one 8-byte word per bin
+ *           and the index set on the device while it runs.
+ * Errors: BAD_ARG, NOT_INJECTIVE (no candidate of some component's list is
+ * injective), OOM, CUDA, TIMEOUT (a bounded device-side retry loop gave up).
+ */
+int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r, const int64_t* n, const int64_t* cand,
+                           int64_t ncand, int64_t* Z_out, int* fixed, int device);
+
 /* Human-readable name of a status code (static storage). */
 const char* lsp_strerror(int code);
 

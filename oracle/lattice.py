@@ -212,3 +212,38 @@ def explicit_table(index_set: np.ndarray, Z, n) -> np.ndarray:
     H = np.zeros_like(I)
     H[chi] = I
     return H
+
+
+# --------------------------------------------------------------------------
+# Component-by-component reconstructing lattice (Sec. 3.1's CBC search, with
+# injectivity of h -> bin on the index set, Def. 2 / Thm 1(iii), as the test)
+# --------------------------------------------------------------------------
+def cbc_reconstructing(index_set: np.ndarray, n, candidates) -> Tuple[np.ndarray, int]:
+    """Component 0 fixed to 1 (rank 1) or (1, 0) (rank 2); component j takes the first
+    candidate c of its list for which the bins of the distinct projections
+    (h_0, ..., h_j) of the index set are distinct.
+
+    candidates: array (d - 1, T, r); returns (Z of shape (d, r), number of components
+    fixed).  When some component has no injective candidate, Z holds zeros from it on.
+    """
+    I = np.asarray(index_set, dtype=np.int64)
+    nt = tuple(int(x) for x in np.atleast_1d(n))
+    r = len(nt)
+    d = I.shape[1]
+    cand = np.asarray(candidates, dtype=np.int64).reshape(d - 1, -1, r)
+    Z = np.zeros((d, r), dtype=np.int64)
+    Z[0, 0] = 1
+    for j in range(1, d):
+        proj = np.unique(I[:, : j + 1], axis=0)
+        for c in cand[j - 1]:
+            Zj = Z[: j + 1].copy()
+            Zj[j] = c
+            chi = np.zeros(proj.shape[0], dtype=np.int64)
+            for i, ni in enumerate(nt):
+                chi = chi * ni + (proj @ Zj[:, i]) % ni
+            if np.unique(chi).size == chi.size:
+                Z[j] = c
+                break
+        else:
+            return Z, j
+    return Z, d

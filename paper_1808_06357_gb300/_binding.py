@@ -61,6 +61,7 @@ def _declare(lib):
         "lsp_batch_status": (I, [P, P]),
         "lsp_adjoint": (I, [P, D, I64, P, P, P, I64, P]),
         "lsp_strang_steps_noalloc": (I, [I, I64, D, D, I64, P, P, P, P]),
+        "lsp_cbc_reconstructing": (I, [P, I64, I, I, P, P, I64, P, C.POINTER(C.c_int), I]),
         "lsp_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -338,3 +339,26 @@ def adjoint(plan: Plan, dt: float, nsteps: int, lamT, grad_v, grad_u0, ckpt_stri
     gu, _ = _buf(grad_u0, output=True)
     _check(plan._lib.lsp_adjoint(plan.handle, float(dt), int(nsteps), lp, gv, gu, int(ckpt_stride),
                                  _stream_ptr(stream)), "lsp_adjoint")
+
+
+def cbc_reconstructing(index_set, n, candidates, device: int = 0):
+    """lsp_cbc_reconstructing: generating vectors built component by component on the GPU.
+
+    index_set (m, d) ints; n an int (rank 1) or (n1, n2); candidates (d - 1, T, r) ints.
+    Returns (Z, fixed): Z of shape (d, r) and the number of components fixed (d on
+    success; fewer when a component's list held no injective candidate).
+    """
+    lib = load_library()
+    I = np.ascontiguousarray(np.asarray(index_set), dtype=np.int32)
+    nt = np.ascontiguousarray(np.atleast_1d(np.asarray(n, dtype=np.int64)))
+    r = int(nt.size)
+    m, d = I.shape
+    cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int64).reshape(max(d - 1, 0), -1, r))
+    Z = np.zeros((d, r), dtype=np.int64)
+    fixed = C.c_int(0)
+    rc = lib.lsp_cbc_reconstructing(C.c_void_p(I.ctypes.data), int(m), int(d), r, C.c_void_p(nt.ctypes.data),
+                                    C.c_void_p(cand.ctypes.data), int(cand.shape[1]) if d > 1 else 0,
+                                    C.c_void_p(Z.ctypes.data), C.byref(fixed), int(device))
+    if rc != -3:                                   # NOT_INJECTIVE is an answer, not a failure
+        _check(rc, "lsp_cbc_reconstructing")
+    return Z, int(fixed.value)

@@ -173,3 +173,59 @@ def test_table1_generating_vectors_are_units():
         z = np.array([int(x) for x in row[2:]], dtype=np.int64)
         assert z.size >= d and z[0] == 1
         assert np.all(z % 2 == 1)
+
+
+# ---------------------------------------------------------------------------
+# component-by-component reconstructing lattice (Sec. 3.1 search, Def. 2 test)
+# ---------------------------------------------------------------------------
+def _collides(proj, z, n):
+    """Pure-Python pair search: two distinct projected rows with the same bin."""
+    nt = [int(x) for x in np.atleast_1d(n)]
+    rows = sorted({tuple(int(v) for v in p) for p in proj})
+    seen = {}
+    for p in rows:
+        key = tuple(sum(p[i] * int(z[i][q]) for i in range(len(p))) % nt[q] for q in range(len(nt)))
+        if key in seen:
+            return True
+        seen[key] = p
+    return False
+
+
+@pytest.mark.parametrize("n", [128, (16, 16), 192])
+def test_cbc_accepts_first_injective_candidate_brute_force(n):
+    import workloads as w
+    rng = np.random.default_rng(5)
+    I = rng.integers(-3, 4, size=(30, 3))
+    I = np.concatenate([I, I[:5]])                       # repeated rows are allowed
+    r = len(np.atleast_1d(n))
+    cand = w.cbc_candidates(3, n, 60, w.Rng(2, 11))
+    Z, fixed = L.cbc_reconstructing(I, n, cand)
+    assert fixed == 3
+    assert Z[0, 0] == 1 and (r == 1 or Z[0, 1] == 0)
+    rejected = 0
+    for j in (1, 2):
+        proj = I[:, : j + 1]
+        t = next(t for t in range(cand.shape[1]) if np.array_equal(cand[j - 1, t], Z[j]))
+        rejected += t
+        for tt in range(t):                               # every earlier candidate collides
+            zz = np.concatenate([Z[:j], cand[j - 1, tt][None]])
+            assert _collides(proj, zz, n)
+        assert not _collides(proj, Z[: j + 1], n)
+    assert rejected >= 15                                 # the search passed over colliding candidates
+    assert L.is_anti_aliasing(np.unique(I, axis=0), Z[:, 0] if r == 1 else Z, n)
+
+
+def test_cbc_regular_grid_closed_form():
+    """The box {0..a-1}^d is mapped injectively by z = (1, a, a^2, ...) mod a^d (mixed radix);
+    z_j = 1 merges (1, 0, ..) and (0, 1, ..), so the search passes over it."""
+    a, d = 4, 3
+    I = np.array(np.meshgrid(*[np.arange(a)] * d, indexing="ij")).reshape(d, -1).T
+    cand = np.array([[[1], [a]], [[a], [a * a]]])
+    Z, fixed = L.cbc_reconstructing(I, a ** d, cand)
+    assert fixed == d and list(Z[:, 0]) == [1, a, a * a]
+
+
+def test_cbc_reports_a_component_without_injective_candidate():
+    I = np.array([[0, 0], [1, 0], [0, 1]])
+    Z, fixed = L.cbc_reconstructing(I, 8, np.array([[[1], [9]]]))    # 9 = 1 mod 8: (1,0), (0,1) share a bin
+    assert fixed == 1 and list(Z[:, 0]) == [1, 0]

@@ -226,6 +226,22 @@ def reconstructing_rank1(index_set: np.ndarray, n: int, rng: Rng,
     return np.array(z, dtype=np.int64)
 
 
+def cbc_candidates(d: int, n, count: int, rng: Rng) -> np.ndarray:
+    """Seeded candidate lists for a component-by-component search: (d - 1, count, r)
+    units modulo each n_i (odd numbers when n_i is a power of two)."""
+    nt = [int(x) for x in np.atleast_1d(n)]
+    out = np.zeros((d - 1, count, len(nt)), dtype=np.int64)
+    for j in range(d - 1):
+        for t in range(count):
+            for i, ni in enumerate(nt):
+                while True:
+                    c = int(rng.integers(1, 1, ni)[0])
+                    if math.gcd(c, ni) == 1:
+                        break
+                out[j, t, i] = c
+    return out
+
+
 def reconstructing_rank2(index_set: np.ndarray, n1: int, n2: int, rng: Rng,
                          tries: int = 4000) -> np.ndarray:
     """Seeded search for Z = (z_1, z_2) with h -> (h.z_1 mod n1, h.z_2 mod n2) injective on I.
