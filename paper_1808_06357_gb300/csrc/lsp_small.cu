@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 4)) small_line_kernel(const Small
   using G = Line<T, NT, LOGN, true>;
   constexpr int LR1 = G::LOGR1, R1 = G::R1;
   const SmallDesc<T>& S = D[blockIdx.x];
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   if (nsteps <= 0) return;
   const T* __restrict__ tw = S.twl;

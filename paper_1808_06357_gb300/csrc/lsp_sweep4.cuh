@@ -224,7 +224,7 @@ __device__ __forceinline__ void sweep4_tile(const S4Inst<T>& I, int t, T* sm, co
       unsigned x = 0;
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        x |= (unsigned)__ldcs(I.kidx + base + Geo::off(bn, jn + ((4 * w + e) << (LOGL - 4)))) << (8 * e);
+        x |= (unsigned)ldtab(I.kidx + base + Geo::off(bn, jn + ((4 * w + e) << (LOGL - 4)))) << (8 * e);
       kb[w] = x;
     }
   } else if constexpr (Ops::KIN) {
