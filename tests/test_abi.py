@@ -64,3 +64,27 @@ def test_binding_resolves_conjugate_views():
     assert np.array_equal(got, [1.0, -2.0, 3.0, 4.0]) and dev == 0
     with pytest.raises(ValueError):
         B._buf(cx, output=True)
+
+
+def test_cbc_argument_checks_without_gpu():
+    """lsp_cbc_reconstructing rejects bad shapes and moduli before touching a device, and reports
+    a missing device as CUDA (never a CPU fallback)."""
+    import numpy as np
+    import pytest
+    import torch
+    import paper_1808_06357_gb300 as lsp
+    I = np.array([[0, 0], [1, 0], [0, 1]])
+    cand = np.array([[[3]]])
+    with pytest.raises(lsp.LspError) as e:
+        lsp.cbc_reconstructing(I, (8, 4, 2), np.zeros((1, 1, 3), dtype=np.int64))   # rank 3
+    assert e.value.code == -1
+    with pytest.raises(lsp.LspError) as e:
+        lsp.cbc_reconstructing(I, 0, cand)                                           # modulus 0
+    assert e.value.code == -1
+    with pytest.raises(lsp.LspError) as e:
+        lsp.cbc_reconstructing(I, (1 << 20, 1 << 12), np.zeros((1, 1, 2), dtype=np.int64))  # 2^32 bins
+    assert e.value.code == -1
+    if not torch.cuda.is_available():
+        with pytest.raises(lsp.LspError) as e:
+            lsp.cbc_reconstructing(I, 8, cand)
+        assert e.value.code == -6
