@@ -326,21 +326,41 @@ def run_ours(args):
     tot_ms = max_over_ranks(sum(ms), world)
     value = world * n * STEPS_PER_CALL * args.steps / (tot_ms / 1e3)
 
-    # roofline of the hot path: algorithmic bytes of all the call's steps over the whole call
-    # (phase-table build and every sweep inside: conservative for any single kernel)
+    # roofline of the whole step: the method's algorithmic bytes of all the call's steps over the
+    # whole call (phase-table build and every sweep inside)
     hbm, src = peaks()
     alg_bytes = 48.0 * n * STEPS_PER_CALL                # 6 s per point-step, s = 8 B (c64)
     kern_s = statistics.mean(ms) / 1e3
-    achieved = alg_bytes / kern_s / 1e9
-    traffic = None
+    step_achieved = alg_bytes / kern_s / 1e9
+    step_traffic = None
+    rec = None
     if args.log2n == 22 and STEPS_PER_CALL == 1000:
         # DRAM bytes of one call from committed ncu records (None once the kernel sources changed)
         if path == lsp.PATH_MULTIPASS:
             rec = traffic_record("c64_n2p22", "mp_persistent")
-            traffic = rec.get("bytes_per_launch") if rec else None
+            step_traffic = rec.get("bytes_per_launch") if rec else None
         elif path == lsp.PATH_RANK1_4SWEEP:
             rec = traffic_record("c64_n2p22_4sweep", "sweep4_rank1")
-            traffic = rec.get("bytes_per_call_1000_steps") if rec else None
+            step_traffic = rec.get("bytes_per_call_1000_steps") if rec else None
+    # roofline of the dominant kernel.  Two-sweep path: the persistent kernel is the call (one
+    # launch runs all its sweeps).  Four-sweep path: the K sweep (DFT_4096, K, IDFT_4096; 31 % of
+    # the step), algorithmic bytes 24 per point (state read and written, the K table), its mean
+    # launch time taken live by lsp_sweep_times (CUDA events on the launching stream, 64 steps).
+    if path == lsp.PATH_RANK1_4SWEEP:
+        sw = plan.sweep_times(inst.dt, 64, stream=stream)
+        k_bytes = 24.0 * n
+        k_traffic = None
+        if rec:
+            z = rec.get("per_kind_mid_step", {}).get("14")
+            k_traffic = z["dram_read"] + z["dram_write"] if z else None
+        kernel = {"name": "sweep4 K sweep (Z: DFT_4096, K by byte index, IDFT_4096)", "ms_per_launch": sw["K"],
+                  "alg_bytes_per_launch": k_bytes, "sweep_ms": sw}
+        achieved = k_bytes / (sw["K"] / 1e3) / 1e9
+        traffic = k_traffic
+    else:
+        kernel = {"name": "mp_persistent (all 2N-1 sweeps of a call in one launch)",
+                  "ms_per_launch": statistics.mean(ms), "alg_bytes_per_launch": alg_bytes}
+        achieved, traffic = step_achieved, step_traffic
     launches = {lsp.PATH_MULTIPASS: 5, lsp.PATH_RANK1_4SWEEP: 3 + 4 * STEPS_PER_CALL}.get(path, 0)
 
     # complex128 side measurement on the same workload
@@ -420,8 +440,10 @@ def run_ours(args):
                        "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
                        "autotune_steps": min(100, STEPS_PER_CALL)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
-                         "alg_bytes_per_point_step": 48},
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": src, "kernel": kernel,
+                         "step": {"achieved": step_achieved, "frac": step_achieved / hbm, "traffic": step_traffic,
+                                  "alg_bytes_per_point_step": 48,
+                                  "what": "the method's 48 B per point-step over the whole timed call"}},
             "complex128": c128,
             "batched": batched,
             "rank2": rank2,

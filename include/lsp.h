@@ -325,6 +325,17 @@ int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, double dt, int64
 int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r, const int64_t* n, const int64_t* cand,
                            int64_t ncand, int64_t* Z_out, int* fixed, int device);
 
+/*
+ * lsp_sweep_times -- per-sweep durations of the four-sweep paths (2 and 3):
+ * nsteps (2 .. 4096) Strang steps of size dt on a scratch copy of the state,
+ * once untimed, then again as plain launches with a CUDA event after each;
+ * ms[0..3] (host) = mean duration in ms of the P sweep between steps (rows /
+ * X), the A / Y sweep, the K sweep (B / Z) and the A^-1 / Y^-1 sweep.  The
+ * plan's state is unchanged; its phase tables are rebuilt for dt.
+ * Synchronous.  Errors: BAD_ARG, UNSUPPORTED (other paths), OOM, CUDA, TIMEOUT.
+ */
+int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double* ms);
+
 /* Human-readable name of a status code (static storage). */
 const char* lsp_strerror(int code);
 

@@ -61,6 +61,7 @@ def _declare(lib):
         "lsp_batch_status": (I, [P, P]),
         "lsp_adjoint": (I, [P, D, I64, P, P, P, I64, P]),
         "lsp_strang_steps_noalloc": (I, [I, I64, D, D, I64, P, P, P, P]),
+        "lsp_sweep_times": (I, [P, D, I64, P, P]),
         "lsp_cbc_reconstructing": (I, [P, I64, I, I, P, P, I64, P, C.POINTER(C.c_int), I]),
         "lsp_strerror": (C.c_char_p, [I]),
     }
@@ -260,6 +261,13 @@ class Plan:
 
     def set_path(self, path: int):
         _check(self._lib.lsp_plan_set_path(self._h, int(path)), "lsp_plan_set_path")
+
+    def sweep_times(self, dt: float, nsteps: int, stream=None) -> dict:
+        """lsp_sweep_times: mean ms per launch of the P, A / Y, K and A^-1 / Y^-1 sweeps (four-sweep paths)."""
+        ms = np.zeros(4, dtype=np.float64)
+        _check(self._lib.lsp_sweep_times(self.handle, float(dt), int(nsteps), _stream_ptr(stream),
+                                         C.c_void_p(ms.ctypes.data)), "lsp_sweep_times")
+        return dict(zip(("P", "A", "K", "A_inv"), (float(x) for x in ms)))
 
     def autotune(self, dt: float, nsteps: int, stream=None):
         """Time nsteps steps on every available path, keep the fastest; returns (path, {path: ms})."""

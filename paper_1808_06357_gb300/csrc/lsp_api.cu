@@ -554,6 +554,12 @@ int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
 
 using namespace lsp;
 
+namespace lsp {
+// lsp_sweep4_host.cu: nsteps four-sweep steps on `state` with an event after each launch;
+// mean duration (ms) of the P, A / Y, K and A^-1 / Y^-1 sweeps
+int s4_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms);
+}  // namespace lsp
+
 extern "C" {
 
 const char* lsp_strerror(int code) {
@@ -938,6 +944,29 @@ int lsp_plan_set_path(lsp_plan p, int path) {
   if (cudaDeviceSynchronize() != cudaSuccess) return LSP_ERR_CUDA;
   int rc = setup_path(p, path);
   if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = LSP_ERR_CUDA;
+  return rc;
+}
+
+int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double* ms) {
+  if (!p || !ms || nsteps < 2 || nsteps > 4096 || !isfinite(dt)) return LSP_ERR_BAD_ARG;
+  if (p->path != kPathRank2 && p->path != kPathRank1x4) return LSP_ERR_UNSUPPORTED;
+  if (*p->err_host != 0) return *p->err_host;
+  DeviceGuard g(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->ntot * csize(p->prec);
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, bytes) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
+  int rc = build_phase_tables(p, dt, s);
+  if (!rc && cudaMemcpyAsync(scratch, p->u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = LSP_ERR_CUDA;
+  double warm[4];
+  if (!rc) rc = s4_sweep_times(p, scratch, nsteps, s, warm);          // warm-up: every kernel once
+  if (!rc) rc = s4_sweep_times(p, scratch, nsteps, s, ms);
+  if (!rc) {
+    int err = 0;
+    if (cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = LSP_ERR_CUDA;
+    else if (err) rc = err;
+  }
+  cudaFree(scratch);
   return rc;
 }
 

@@ -106,6 +106,65 @@ template <typename T> static int s4_launch_steps(lsp_plan p, const S4Inst<T>& I,
   return rc;
 }
 
+// The same launches as s4_launch_steps with an event recorded after each one, for
+// per-sweep durations: ms[0] P sweeps between steps (rows / X mid), ms[1] A / Y,
+// ms[2] the K sweep (B / Z), ms[3] A^-1 / Y^-1, each the mean over the call.
+template <typename T> static int s4_sweep_times_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s,
+                                                     double* ms) {
+  S4Kernels K;
+  if (!s4_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
+  const S4Inst<T> I = s4_inst<T>(p, state);
+  const bool r2 = p->path == kPathRank2;
+  const int head = r2 ? kR2Head : kXHead, mid = r2 ? kR2Mid : kXMid, tail = r2 ? kR2Tail : kXTail;
+  const int pg = r2 ? 0 : 1;
+  const int seq[3] = {r2 ? kR2A : kY, r2 ? kR2B : kZ, r2 ? kR2AInv : kYInv};
+  const int geo[3] = {r2 ? 1 : 2, r2 ? 2 : 0, r2 ? 1 : 2};
+  const void* kin = I.kidx ? K.k_kidx : K.k[seq[1]];
+  std::vector<cudaEvent_t> ev((size_t)(4 * nsteps + 2), nullptr);
+  int rc = LSP_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
+  std::vector<int> kind;                                // sweep class of launch i (-1: head / tail)
+  size_t k = 0;
+  if (!rc) rc = cudaEventRecord(ev[k++], s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
+  for (int64_t st = 0; st < nsteps && !rc; ++st) {
+    rc = s4_launch<T>(K.k[st == 0 ? head : mid], I, K.ntiles[pg], s);
+    kind.push_back(st == 0 ? -1 : 0);
+    if (!rc) rc = cudaEventRecord(ev[k++], s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
+    for (int i = 0; i < 3 && !rc; ++i) {
+      rc = s4_launch<T>(i == 1 ? kin : K.k[seq[i]], I, K.ntiles[geo[i]], s);
+      kind.push_back(1 + i);
+      if (!rc) rc = cudaEventRecord(ev[k++], s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
+    }
+  }
+  if (!rc) {
+    rc = s4_launch<T>(K.k[tail], I, K.ntiles[pg], s);
+    kind.push_back(-1);
+    if (!rc) rc = cudaEventRecord(ev[k++], s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
+  }
+  if (!rc && cudaEventSynchronize(ev[k - 1]) != cudaSuccess) rc = LSP_ERR_CUDA;
+  if (!rc) {
+    double sum[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < kind.size(); ++i) {
+      if (kind[i] < 0) continue;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      sum[kind[i]] += t;
+      cnt[kind[i]] += 1;
+    }
+    for (int c = 0; c < 4; ++c) ms[c] = cnt[c] ? sum[c] / cnt[c] : -1.0;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+int s4_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms) {
+  return p->prec == LSP_C64 ? s4_sweep_times_impl<float2>(p, state, nsteps, s, ms)
+                            : s4_sweep_times_impl<double2>(p, state, nsteps, s, ms);
+}
+
 constexpr int64_t kGraphMinSteps = 16;
 
 // The 4 N + 1 launches of a call, captured once as a CUDA graph on a private

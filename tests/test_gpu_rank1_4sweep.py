@@ -174,3 +174,21 @@ def test_c2_1000_steps_complex64_against_complex128(lib):
     err = float(torch.linalg.norm(out["c64"][0] - out["c128"][0]) / torch.linalg.norm(out["c128"][0]))
     print(f"C2 1000 steps: complex64 four-sweep rel-L2 {err:.3e}, norm drift {out['c64'][1]:.3e}")
     assert err < 5e-5 and out["c64"][1] < 5e-5 and out["c128"][1] < 1e-12
+
+
+def test_sweep_times_leave_the_state(lib):
+    """lsp_sweep_times: positive per-sweep durations on the four-sweep paths, the plan's state
+    untouched, UNSUPPORTED on the two-sweep path."""
+    import torch
+    inst = w.c2(20)
+    plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64")
+    plan.set_path(lib.PATH_RANK1_4SWEEP)
+    u0 = torch.randn(inst.npoints, dtype=torch.complex64, device="cuda")
+    plan.set_state(u0)
+    t = plan.sweep_times(inst.dt, 8)
+    assert set(t) == {"P", "A", "K", "A_inv"} and all(x > 0 for x in t.values())
+    assert torch.equal(plan.get_state(), u0)
+    plan.set_path(lib.PATH_MULTIPASS)
+    with pytest.raises(lib.LspError) as e:
+        plan.sweep_times(inst.dt, 8)
+    assert e.value.code == -8
