@@ -13,7 +13,10 @@ The oracle is a plain, slow, obviously-correct restatement of what the paper
   property (eqs. dual, char), anti-aliasing sets (Def. 2) and the minimal-l2
   representative per bin (Lemma 4, eq. hrepresenter), both by the paper's
   enumerate-sort-greedy recipe (Sec. 3.1) and by an exact min-plus dynamic
-  programme over residues.
+  programme over residues; and a component-by-component search for a lattice
+  that maps a given index set injectively (Sec. 3.1's CBC construction with
+  Def. 2's injectivity as the acceptance test), pinned by pure-Python pair
+  searches and the regular grid's mixed-radix generating vector.
 * ``oracle.strang`` -- lattice-rule coefficients (eq. approx_uhat), the
   Strang step of eq. StrangTDSE / Algorithm 1 in physical form, the norm,
   energy and overlap observables (Sec. 3.3), the adjoint gradient of
