@@ -238,10 +238,15 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
 
 /*
  * Batched stepping: many independent instances (same precision and device)
- * advanced together.  Instances on the SMEM-resident path share one launch
- * (one CTA each); rank-1 multipass instances are grouped by lattice size, one
- * persistent cooperative launch per size per call; rank-2 multipass instances
- * (each large enough to fill the device) are stepped one after another.
+ * advanced together.  Instances on the SMEM-resident path run one CTA each:
+ * one launch per power-of-two size on the register-resident line kernel and
+ * one for all others; rank-1 two-sweep instances are grouped by lattice size,
+ * one persistent cooperative launch per size per call; rank-1 four-sweep
+ * instances of up to 2^22 points are grouped by size, one launch per sweep over
+ * all the group's tiles, replayed as a CUDA graph for calls of 16 steps or more;
+ * other four-sweep instances (rank 2, larger rank 1; each fills the device)
+ * are stepped one after another.  A plan may belong to several batches, but a
+ * call must not overlap another call on the same plans.
  *   lsp_batch_create  plans: `count` plan handles (host array, borrowed: the
  *                     plans must outlive the batch).  Errors: BAD_ARG, OOM, CUDA,
  *                     UNSUPPORTED (mixed precision or device).
