@@ -261,6 +261,8 @@ static int s4_class_sync_impl(lsp_batch_s::S4Class& c, const std::vector<lsp_pla
   }
   *changed = h != c.inst_host;
   if (!*changed) return LSP_OK;
+  // launches of an earlier call may still read the old descriptors: let them finish first
+  if (c.inst) LSP_CUDA_TRY(cudaDeviceSynchronize());
   if (!c.inst && cudaMalloc(&c.inst, h.size()) != cudaSuccess) return LSP_ERR_OOM;
   LSP_CUDA_TRY(cudaMemcpy(c.inst, h.data(), h.size(), cudaMemcpyHostToDevice));
   c.inst_host = h;
