@@ -265,7 +265,6 @@ def run_ours(args):
     import torch
 
     import paper_1808_06357_gb300 as lsp
-    from oracle import lattice as L  # only for the input points of the bounded CPU baseline
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
