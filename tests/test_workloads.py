@@ -77,3 +77,17 @@ def test_paper_initial_conditions():
     assert abs(np.mean(np.abs(h) ** 2) - 1) < 1e-12 and np.all(h.real >= 0)
     far = np.abs(P[:, 1] - 0.5) > np.sqrt(gamma) / 4 + 1e-12
     assert np.all(h[far] == 0)
+
+
+def test_cbc_candidates_are_seeded_units():
+    """Candidate lists for the component-by-component search: shape (d - 1, count, r), every entry a
+    unit modulo its n_i, the same lists for the same seed and different ones for another."""
+    import math
+    a = w.cbc_candidates(4, (1 << 10, 1 << 6), 50, w.Rng(3, 21))
+    b = w.cbc_candidates(4, (1 << 10, 1 << 6), 50, w.Rng(3, 21))
+    c = w.cbc_candidates(4, (1 << 10, 1 << 6), 50, w.Rng(4, 21))
+    assert a.shape == (3, 50, 2) and np.array_equal(a, b) and not np.array_equal(a, c)
+    assert all(math.gcd(int(x), 1 << 10) == 1 for x in a[..., 0].ravel())
+    assert all(math.gcd(int(x), 1 << 6) == 1 for x in a[..., 1].ravel())
+    r1 = w.cbc_candidates(3, 768, 40, w.Rng(0, 21))
+    assert r1.shape == (2, 40, 1) and all(math.gcd(int(x), 768) == 1 for x in r1.ravel())
