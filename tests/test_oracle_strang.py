@@ -326,3 +326,36 @@ def test_composed_strang_fourth_order_against_dense_propagator():
     assert errs[-1] < 1e-6
     for r in ratios:
         assert 13 < r < 19, (errs, ratios)
+
+
+@pytest.mark.parametrize("Z,n", CASES)
+@pytest.mark.parametrize("gamma,c0", [(0.5, 0.0), (0.1, 1.7), (2.0, -0.6)])
+def test_energy_of_plane_waves_closed_form(Z, n, gamma, c0):
+    """Sec. 3.3 energy <H u, u>, H = -(gamma/2) Lap + v / gamma, on a trigonometric state.
+
+    For u = sum_j c_j exp(2 pi i h_j . x) with distinct anti-aliasing vectors h_j and a
+    constant potential v = c0, the Laplacian acts on each plane wave by -4 pi^2 ||h_j||^2
+    and the waves are orthonormal under the lattice rule, so
+        E = sum_j |c_j|^2 (2 pi^2 gamma ||h_j||^2 + c0 / gamma)
+    exactly.  This fixes the absolute scale of both terms (a common factor would
+    pass every conservation test)."""
+    dp, H, P = _setup(Z, n)
+    rng = np.random.default_rng(11)
+    for k in (1, 3):
+        idx = rng.choice(H.shape[0], size=k, replace=False)
+        hs = H[idx]
+        c = _rand_c(rng, k)
+        u = np.exp(2j * np.pi * (P @ hs.T)) @ c
+        v = np.full(P.shape[0], c0)
+        h2 = np.sum(hs.astype(np.float64) ** 2, axis=1)
+        expect = float(np.sum(np.abs(c) ** 2 * (2.0 * np.pi ** 2 * gamma * h2 + c0 / gamma)))
+        got = S.energy(u, v, dp, n, gamma)
+        assert abs(got - expect) <= 1e-11 * max(1.0, abs(expect)), (got, expect)
+    # a single zero-frequency wave isolates the potential term, a single wave with v = 0
+    # the kinetic term
+    u0 = np.full(P.shape[0], 2.0 + 0j)
+    assert abs(S.energy(u0, np.full(P.shape[0], c0), dp, n, gamma) - 4.0 * c0 / gamma) < 1e-12
+    j = int(np.argmax(np.sum(H.astype(np.float64) ** 2, axis=1)))
+    u1 = np.exp(2j * np.pi * (P @ H[j]))
+    want = 2.0 * np.pi ** 2 * gamma * float(np.sum(H[j].astype(np.float64) ** 2))
+    assert abs(S.energy(u1, np.zeros(P.shape[0]), dp, n, gamma) - want) < 1e-10 * want
