@@ -251,8 +251,11 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
  *                     plans must outlive the batch).  Errors: BAD_ARG, OOM, CUDA,
  *                     UNSUPPORTED (mixed precision or device).
  *   lsp_batch_steps   dt: `count` step sizes (host), one per instance;
- *                     every instance advances nsteps steps.  Errors as
- *                     lsp_strang_steps.
+ *                     every instance advances nsteps steps.  When an instance's
+ *                     device descriptors changed since the last call (e.g. its
+ *                     phase-table form), the new ones are copied on `stream`,
+ *                     ordered after earlier calls on it; such a call cannot be
+ *                     recorded by stream capture.  Errors as lsp_strang_steps.
  */
 int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count);
 int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream);
@@ -294,10 +297,14 @@ int lsp_adjoint(lsp_plan p, double dt, int64_t nsteps, const void* lamT, double*
  *           lsp_index_norms returns for the same lattice).
  *   u       n complex (device), read and overwritten in place.
  * Runs on the current CUDA device, asynchronously on `stream`.  The first call
- * on a device looks up the device address of the array (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call on a device
- * shares the one array and rewrites it completely, so calls that overlap on
- * the GPU (other streams, other threads) race; serialise them.
+ * on a device (nsteps = 0 is enough) looks up the device address of the array
+ * (cudaGetSymbolAddress); with lazy module loading that lookup also loads the
+ * library's module and so reserves the array, which can fail if the device is
+ * full.  Make that first call before the allocation-free phase begins and before
+ * any stream capture.  The address is kept per device for the life of the
+ * process: do not call this after cudaDeviceReset on that device.  Every call
+ * on a device shares the one array and rewrites it completely, so calls that
+ * overlap on the GPU (other streams, other threads) race; serialise them.
  * Errors: BAD_ARG, TOO_LARGE, CUDA.
  */
 int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, double dt, int64_t nsteps,
@@ -314,6 +321,9 @@ int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, double dt, int64
  *   h -> (h_0..h_j).(z_0..z_j) mod n            (rank 1), or
  *   h -> ((h_0..h_j).(z_1..) mod n1) n2 + ((h_0..h_j).(z_2..) mod n2)  (rank 2)
  * is injective on the projection of I onto its first j + 1 coordinates is kept.
+ * Component 0 itself is checked first (distinct values of h_0 must have distinct
+ * residues mod n_1); if that fails the call returns NOT_INJECTIVE with *fixed = 0.
+ * Candidates are reduced mod n_i before use and Z_out holds the reduced values.
  *   I       m x d int32 (host), row-major: the index set (rows may repeat).
  *   r       1 or 2;  n  r moduli (host), with n_1 (n_2) <= 2^31 and the bin
  *           count n (rank 1) or n_1 n_2 (rank 2) <= 2^31.
@@ -340,6 +350,28 @@ int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r, const int6
  * Synchronous.  Errors: BAD_ARG, UNSUPPORTED (other paths), OOM, CUDA, TIMEOUT.
  */
 int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double* ms);
+
+/*
+ * lsp_plan_set_wait_limit -- test hook for failure detection: the number of
+ * polls (~100 ns each) a bounded device-side wait of this plan's kernels (the
+ * grid barrier and the tile-prefetch wait of the persistent two-sweep kernel)
+ * makes before it gives up, sets LSP_ERR_TIMEOUT and returns.  0 restores the
+ * default (2^25 polls, seconds).  A wait that gives up leaves no copy in flight;
+ * lsp_set_state then clears the status.  Not in the paper.
+ * Errors: BAD_ARG (null plan, polls < 0).
+ */
+int lsp_plan_set_wait_limit(lsp_plan p, int64_t polls);
+
+/*
+ * lsp_fma_rate -- measured arithmetic peak of `device` for the bound of the
+ * complex128 path (prec = LSP_C128: FP64 fused multiply-adds) or of FP32 work
+ * (LSP_C64): one launch of independent FMA chains on every SM, timed with CUDA
+ * events after a warm-up launch.  *tflops receives flops per second / 1e12 (an
+ * FMA counts 2), *ms (may be NULL) the launch time.  Synchronous; allocates one
+ * word.  Not in the paper: the denominator of the complex128 roofline.
+ * Errors: BAD_ARG, OOM, CUDA.
+ */
+int lsp_fma_rate(int device, int prec, double* tflops, double* ms);
 
 /* Human-readable name of a status code (static storage). */
 const char* lsp_strerror(int code);

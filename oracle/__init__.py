@@ -21,6 +21,9 @@ The oracle is a plain, slow, obviously-correct restatement of what the paper
   Strang step of eq. StrangTDSE / Algorithm 1 in physical form, the norm,
   energy and overlap observables (Sec. 3.3), the adjoint gradient of
   |<u_T, phi>|^2, and the dense semi-discrete propagator of eq. ode.
+* ``oracle.initial_error`` -- the exact Fourier coefficients of the paper's
+  initial function g1 (closed form through the Faddeeva function) and the
+  initial discretisation error e_total of Sec. 3.4.
 
 Everything runs in IEEE double precision with numpy; numpy.fft is used as the
 FFT primitive.  Parity pins (what fixes each function independently of
@@ -29,4 +32,4 @@ adjoint gradient is not in the paper; it is pinned by central finite
 differences of the oracle's own forward map.
 """
 
-from . import lattice, strang  # noqa: F401
+from . import initial_error, lattice, strang  # noqa: F401

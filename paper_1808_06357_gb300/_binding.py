@@ -63,6 +63,8 @@ def _declare(lib):
         "lsp_strang_steps_noalloc": (I, [I, I64, D, D, I64, P, P, P, P]),
         "lsp_sweep_times": (I, [P, D, I64, P, P]),
         "lsp_cbc_reconstructing": (I, [P, I64, I, I, P, P, I64, P, C.POINTER(C.c_int), I]),
+        "lsp_plan_set_wait_limit": (I, [P, I64]),
+        "lsp_fma_rate": (I, [I, I, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "lsp_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -237,6 +239,10 @@ class Plan:
     def status(self, stream=None) -> int:
         return int(self._lib.lsp_plan_status(self._h, _stream_ptr(stream)))
 
+    def set_wait_limit(self, polls: int):
+        """lsp_plan_set_wait_limit: polls of a bounded device wait before it gives up (0: default)."""
+        _check(self._lib.lsp_plan_set_wait_limit(self._h, int(polls)), "lsp_plan_set_wait_limit")
+
     # -- queries -----------------------------------------------------------
     def lattice_points(self) -> np.ndarray:
         x = np.empty((self.npoints, self.d), dtype=np.float64)
@@ -322,6 +328,14 @@ class Batch:
             pass
 
 
+def fma_rate(prec="c128", device: int = 0):
+    """lsp_fma_rate: measured FMA throughput of the device in TFLOP/s (FP64 for c128, FP32 for c64)."""
+    lib = load_library()
+    t, ms = C.c_double(), C.c_double()
+    _check(lib.lsp_fma_rate(int(device), _prec_code(prec), C.byref(t), C.byref(ms)), "lsp_fma_rate")
+    return float(t.value)
+
+
 def yoshida4():
     """Stage weights (c, 1 - 2c, c), c = 1 / (2 - 2^(1/3)): a fourth-order composition of Strang steps."""
     c = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
@@ -330,14 +344,33 @@ def yoshida4():
 
 def strang_steps_noalloc(u, v, norm2, gamma: float, dt: float, nsteps: int, stream=None):
     """lsp_strang_steps_noalloc: allocation-free Strang steps on device tensors
-    (u complex64/complex128 updated in place, v float64, norm2 int32)."""
+    (u complex64/complex128 updated in place, v float64, norm2 int32, all with
+    u.numel() elements on u's CUDA device).  The kernels take raw pointers, so
+    every argument is checked here: a host array, a shorter or differently typed
+    buffer or a tensor on another device would be read out of bounds."""
+    import torch
+    for name, t in (("u", u), ("v", v), ("norm2", norm2)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device != u.device:
+            raise ValueError(f"{name} is on {t.device}, u on {u.device}")
+    if u.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError(f"u must be complex64 or complex128, not {u.dtype}")
+    if v.dtype != torch.float64:
+        raise ValueError(f"v must be float64, not {v.dtype}")
+    if norm2.dtype != torch.int32:
+        raise ValueError(f"norm2 must be int32, not {norm2.dtype}")
+    n = u.numel()
+    if v.numel() != n or norm2.numel() != n:
+        raise ValueError(f"v ({v.numel()}) and norm2 ({norm2.numel()}) must hold u.numel() = {n} elements")
     lib = load_library()
-    prec = C64 if str(u.dtype).endswith("complex64") else C128
-    up, _ = _buf(u, output=True)
-    vp, _ = _buf(v)
-    np_, _ = _buf(norm2)
-    _check(lib.lsp_strang_steps_noalloc(prec, int(u.numel()), float(gamma), float(dt), int(nsteps), vp, np_, up,
-                                        _stream_ptr(stream)), "lsp_strang_steps_noalloc")
+    prec = C64 if u.dtype == torch.complex64 else C128
+    with torch.cuda.device(u.device):
+        up, _ = _buf(u, output=True)
+        vp, _ = _buf(v)
+        np_, _ = _buf(norm2)
+        _check(lib.lsp_strang_steps_noalloc(prec, int(n), float(gamma), float(dt), int(nsteps), vp, np_, up,
+                                            _stream_ptr(stream)), "lsp_strang_steps_noalloc")
 
 
 def adjoint(plan: Plan, dt: float, nsteps: int, lamT, grad_v, grad_u0, ckpt_stride: int = 0, stream=None):

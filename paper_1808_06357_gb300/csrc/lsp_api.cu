@@ -294,17 +294,6 @@ static long long mulmod(long long a, long long b, long long m) {
   return (long long)(((__int128)a * (__int128)b) % m);
 }
 
-static void factorize(int len, SmallAxis& ax) {
-  ax.nfac = 0;
-  int rem = len;
-  const int pref[] = {16, 8, 4, 2};
-  for (int f : pref)
-    while (rem % f == 0 && ax.nfac < 24) { ax.fac[ax.nfac++] = f; rem /= f; }
-  for (int f = 3; f <= rem && ax.nfac < 24; f += 2)
-    while (rem % f == 0) { ax.fac[ax.nfac++] = f; rem /= f; }
-  if (rem > 1 && ax.nfac < 24) ax.fac[ax.nfac++] = rem;
-}
-
 // One table entry exp(-2 pi i f) (f in turns, reduced to [-1/2, 1/2]) in the
 // multipass tables' form: complex128 (cos, sin); complex64 (cos - 1, sin) with
 // cos - 1 = -2 sin^2(pi f) evaluated without cancellation (see twmul).
@@ -496,7 +485,7 @@ static int setup_path_tables(lsp_plan p, int path) {
     p->axes[i].len = (int)p->n[i];
     p->axes[i].stride = (int)stride;
     stride *= p->n[i];
-    factorize((int)p->n[i], p->axes[i]);
+    if (!factorize_axis((int)p->n[i], p->axes[i])) return LSP_ERR_TOO_LARGE;
   }
   for (int i = 0; i < p->naxes; ++i) {
     p->axes[i].tw_off = (int)(tw.size() / sz);
@@ -945,6 +934,12 @@ int lsp_plan_set_path(lsp_plan p, int path) {
   int rc = setup_path(p, path);
   if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = LSP_ERR_CUDA;
   return rc;
+}
+
+int lsp_plan_set_wait_limit(lsp_plan p, int64_t polls) {
+  if (!p || polls < 0) return LSP_ERR_BAD_ARG;
+  p->spin_limit = polls == 0 ? kSpinLimit : (long long)polls;
+  return LSP_OK;
 }
 
 int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double* ms) {

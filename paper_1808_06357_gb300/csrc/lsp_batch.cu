@@ -56,7 +56,7 @@ int s4_batch_steps(lsp_batch b, int64_t nsteps, cudaStream_t s) {
   memcpy(key.data(), &nsteps, sizeof(nsteps));
   for (auto& c : b->s4classes) {
     bool changed = false;
-    int rc = s4_class_sync(c, b->plans, &changed);
+    int rc = s4_class_sync(c, b->plans, &changed, s);
     if (rc) return rc;
     key.insert(key.end(), c.inst_host.begin(), c.inst_host.end());
   }
@@ -124,7 +124,8 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
     c.ids = kv.second;
     int rc = s4_class_init(c, b->plans);
     bool changed = false;
-    if (!rc) rc = s4_class_sync(c, b->plans, &changed);
+    if (!rc) rc = s4_class_sync(c, b->plans, &changed, nullptr);
+    if (!rc && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = LSP_ERR_CUDA;
     if (rc) return fail(rc);
   }
   // SMEM-resident groups

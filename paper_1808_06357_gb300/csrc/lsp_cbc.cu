@@ -77,6 +77,27 @@ extern "C" int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r,
   cudaSetDevice(device);
   std::vector<long long> Z((size_t)d * r, 0);
   Z[0] = 1;                                           // (1) or (1, 0)
+  {
+    // component 0 alone: h_0 -> h_0 mod n_1 must be injective on the distinct values
+    // of h_0 in I (a d = 1 lattice is accepted or rejected by this check only)
+    std::vector<int32_t> h0((size_t)m);
+    for (int64_t i = 0; i < m; ++i) h0[(size_t)i] = I[(size_t)i * d];
+    std::sort(h0.begin(), h0.end());
+    h0.erase(std::unique(h0.begin(), h0.end()), h0.end());
+    if ((long long)h0.size() > n1) {
+      for (int64_t i = 0; i < d * r; ++i) Z_out[i] = 0;
+      if (fixed) *fixed = 0;
+      return LSP_ERR_NOT_INJECTIVE;
+    }
+    std::vector<long long> res(h0.size());
+    for (size_t i = 0; i < h0.size(); ++i) res[i] = ((long long)h0[i] % n1 + n1) % n1;
+    std::sort(res.begin(), res.end());
+    if (std::adjacent_find(res.begin(), res.end()) != res.end()) {
+      for (int64_t i = 0; i < d * r; ++i) Z_out[i] = 0;
+      if (fixed) *fixed = 0;
+      return LSP_ERR_NOT_INJECTIVE;
+    }
+  }
   int32_t* dI = nullptr;
   long long* dZ = nullptr;
   unsigned long long* table = nullptr;
@@ -101,7 +122,9 @@ extern "C" int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r,
       }
       bool found = false;
       for (int64_t t = 0; t < ncand && !found && rc == LSP_OK; ++t) {
-        const int64_t* c = cand + ((size_t)(j - 1) * ncand + t) * r;
+        const int64_t* cr = cand + ((size_t)(j - 1) * ncand + t) * r;
+        // candidates reduced mod n_i (an equivalent lattice; keeps h z products in int64)
+        const int64_t c[2] = {((cr[0] % n1) + n1) % n1, r == 2 ? ((cr[1] % n2) + n2) % n2 : 0};
         if (++tag == 0) {                               // stamps wrapped: clear the table
           if (cudaMemset(table, 0, nbins * sizeof(unsigned long long)) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
           tag = 1;

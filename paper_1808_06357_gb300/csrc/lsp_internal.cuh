@@ -49,6 +49,33 @@ struct SmallAxis {
   int tw_off;       // offset of this axis' twiddle table in tw_small
 };
 
+// Radix factors of an axis of length len for the SMEM-resident passes: 16, 8, 4,
+// 2 first, then odd factors in increasing order (a prime above the last tried
+// factor stays whole).  False when the factors would not fit ax.fac.
+inline bool factorize_axis(int len, SmallAxis& ax) {
+  const int cap = (int)(sizeof(ax.fac) / sizeof(ax.fac[0]));
+  ax.nfac = 0;
+  int rem = len;
+  const int pref[] = {16, 8, 4, 2};
+  for (int f : pref)
+    while (rem % f == 0) {
+      if (ax.nfac >= cap) return false;
+      ax.fac[ax.nfac++] = f;
+      rem /= f;
+    }
+  for (int f = 3; f <= rem; f += 2)
+    while (rem % f == 0) {
+      if (ax.nfac >= cap) return false;
+      ax.fac[ax.nfac++] = f;
+      rem /= f;
+    }
+  if (rem > 1) {
+    if (ax.nfac >= cap) return false;
+    ax.fac[ax.nfac++] = rem;
+  }
+  return true;
+}
+
 }  // namespace lsp
 
 struct lsp_plan_s {
@@ -106,6 +133,7 @@ struct lsp_plan_s {
   cudaStream_t capture = nullptr;   // private stream for graph capture
   double tables_dt = 0.0;     // dt of the current phase tables (NaN: none)
   bool tables_valid = false;
+  long long spin_limit = lsp::kSpinLimit;   // polls of a bounded device wait (lsp_plan_set_wait_limit)
 };
 
 struct lsp_batch_s {
@@ -322,7 +350,7 @@ int s4_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 // the launches of nsteps steps; release.
 bool s4_batchable(lsp_plan p);
 int s4_class_init(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans);
-int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed);
+int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed, cudaStream_t s);
 int s4_class_steps(const lsp_batch_s::S4Class& c, int prec, int64_t nsteps, cudaStream_t s);
 void s4_class_free(lsp_batch_s::S4Class& c);
 int s4_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)

@@ -53,6 +53,7 @@ template <typename T> struct MPParams {
   int kind;                 // single-sweep kernels only
   unsigned* bar;
   int* err;
+  long long spin_limit;     // polls of a bounded wait before it gives up (persistent kernel)
 };
 
 #ifndef LSP_MINB_C64
@@ -298,7 +299,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& target, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& target, int* err, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -309,7 +310,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& target, in
     long long spins = 0;
     while ((int)(ld_acquire(bar) - target) < 0) {
       if (*(volatile int*)err != 0) { ok = 0; break; }
-      if (++spins > kSpinLimit) { atomicCAS(err, 0, LSP_ERR_TIMEOUT); ok = 0; break; }
+      if (++spins > limit) { atomicCAS(err, 0, LSP_ERR_TIMEOUT); ok = 0; break; }
       __nanosleep(32);
     }
     __threadfence();
@@ -349,11 +350,13 @@ __device__ __forceinline__ void prefetch_tile(const MPInst<T>& I, int tile, T* p
   }
 }
 
-// Bounded wait on the prefetch mbarrier; false (error word set) on expiry.
-__device__ __forceinline__ bool wait_prefetch(unsigned long long* mb, unsigned parity, int* err) {
+// Bounded wait on the prefetch mbarrier; false (error word set) after `limit` polls.
+// The copy in flight is then still waited for (bounded by kSpinLimit polls) so that
+// no copy lands in shared memory after the CTA has left.
+__device__ __forceinline__ bool wait_prefetch(unsigned long long* mb, unsigned parity, int* err, long long limit) {
   long long spins = 0;
   while (!mbar_try_wait(mb, parity)) {
-    if (++spins > kSpinLimit) {
+    if (++spins > limit) {
       atomicCAS(err, 0, LSP_ERR_TIMEOUT);
       // keep waiting (bounded again) so that no copy is in flight when the CTA leaves
       for (long long k = 0; k < kSpinLimit && !mbar_try_wait(mb, parity); ++k) __nanosleep(64);
@@ -389,7 +392,7 @@ __device__ __forceinline__ bool persistent_sweep(const MPParams<T>& P, T* smem, 
   fence_proxy_async();
   prefetch_tile<T, NT, M, COL>(P.inst[i], l, pre, mb);
   for (; t < total; t += stride) {
-    if (!wait_prefetch(mb, parity, P.err)) fail[w] = 1;
+    if (!wait_prefetch(mb, parity, P.err, P.spin_limit)) fail[w] = 1;
     G::sync();
     if (fail[w]) return false;
     parity ^= 1u;
@@ -436,9 +439,9 @@ __global__ void __launch_bounds__(NT * Cfg<T>::NW, Cfg<T>::MINB) mp_persistent(c
   for (long long step = 0; step < P.nsteps; ++step) {
     persistent_sweep<T, NT, M, false>(P, smem, twr, &mb[w], parity, fail);
     if (step + 1 == P.nsteps) break;
-    if (!grid_barrier(P.bar, target, P.err)) return;
+    if (!grid_barrier(P.bar, target, P.err, P.spin_limit)) return;
     persistent_sweep<T, NT, M, true>(P, smem, twc, &mb[w], parity, fail);
-    if (!grid_barrier(P.bar, target, P.err)) return;
+    if (!grid_barrier(P.bar, target, P.err, P.spin_limit)) return;
   }
 }
 

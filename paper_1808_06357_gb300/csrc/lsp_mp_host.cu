@@ -63,7 +63,8 @@ template <typename T> static int coresident(const void* fn, size_t smem, int& gr
 
 template <typename T>
 int launch_persistent(int m, const MPInst<T>* dinst, const int2* colmap, const int2* rowmap, int ninst,
-                      int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
+                      int total_col, int total_row, int64_t nsteps, unsigned* bar, int* err, long long spin_limit,
+                      cudaStream_t s) {
   MPKernels k;
   if (!kernels_for(sizeof(T) == 8 ? LSP_C64 : LSP_C128, m, &k)) return LSP_ERR_TOO_LARGE;
   constexpr int NT = Cfg<T>::NT * Cfg<T>::NW;
@@ -72,7 +73,7 @@ int launch_persistent(int m, const MPInst<T>* dinst, const int2* colmap, const i
   int rc = coresident<T>(k.persistent, smem, grid);
   if (rc) return rc;
   grid = std::min(grid, (std::max(total_col, total_row) + Cfg<T>::NW - 1) / Cfg<T>::NW);
-  MPParams<T> P{dinst, colmap, rowmap, ninst, total_col, total_row, (long long)nsteps, 0, bar, err};
+  MPParams<T> P{dinst, colmap, rowmap, ninst, total_col, total_row, (long long)nsteps, 0, bar, err, spin_limit};
   LSP_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
   void* args[] = {&P};
   LSP_CUDA_TRY(cudaLaunchCooperativeKernel(k.persistent, dim3(grid), dim3(NT), args, smem, s));
@@ -91,7 +92,7 @@ int launch_sweep(int m, const MPInst<T>* dinst, const int2* colmap, const int2* 
   if (rc) return rc;
   const bool col = kind != kRow && kind != kRowFwd;
   grid = std::min(grid, ((col ? total_col : total_row) + Cfg<T>::NW - 1) / Cfg<T>::NW);
-  MPParams<T> P{dinst, colmap, rowmap, ninst, total_col, total_row, 0, kind, nullptr, nullptr};
+  MPParams<T> P{dinst, colmap, rowmap, ninst, total_col, total_row, 0, kind, nullptr, nullptr, kSpinLimit};
   void* args[] = {&P};
   LSP_CUDA_TRY(cudaLaunchKernel(k.sweep[kind], dim3(grid), dim3(NT), args, smem, s));
   return LSP_OK;
@@ -122,8 +123,9 @@ int multipass_upload_desc(lsp_plan p, cudaStream_t s) {
 // Sweeps 1..2N-1 of N steps (row, mid, ..., row): one persistent cooperative launch.
 template <typename T>
 static int middle_sweeps(int m, const MPInst<T>* d, const int2* colmap, const int2* rowmap, int ninst, int total_col,
-                         int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s) {
-  return launch_persistent<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, s);
+                         int total_row, int64_t nsteps, unsigned* bar, int* err, cudaStream_t s,
+                         long long spin_limit = kSpinLimit) {
+  return launch_persistent<T>(m, d, colmap, rowmap, ninst, total_col, total_row, nsteps, bar, err, spin_limit, s);
 }
 
 // head sweep, sweeps 1..2N-1, tail sweep
@@ -132,7 +134,8 @@ static int steps_impl(lsp_plan p, int64_t nsteps, cudaStream_t s) {
   MPInst<T> I = make_inst<T>(p, nullptr);
   const MPInst<T>* d = (const MPInst<T>*)p->desc;
   int rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kHead, s);
-  if (!rc) rc = middle_sweeps<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
+  if (!rc) rc = middle_sweeps<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s,
+                                 p->spin_limit);
   if (!rc) rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kTail, s);
   return rc;
 }
@@ -146,7 +149,8 @@ static int steps_on_impl(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s
   MPInst<T>* d = (MPInst<T>*)p->desc + 2;
   LSP_CUDA_TRY(cudaMemcpyAsync(d, &I, sizeof(I), cudaMemcpyHostToDevice, s));
   int rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kHead, s);
-  if (!rc) rc = middle_sweeps<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s);
+  if (!rc) rc = middle_sweeps<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, nsteps, p->bar, p->err, s,
+                                 p->spin_limit);
   if (!rc) rc = launch_sweep<T>(p->logn, d, nullptr, nullptr, 1, I.ncol, I.nrow, kTail, s);
   return rc;
 }

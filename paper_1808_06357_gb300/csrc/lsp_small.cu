@@ -95,25 +95,12 @@ __device__ T* small_dft(const SmallDesc<T>& S, T* a, T* b) {
   return src;
 }
 
+// The Strang loop on a state already in shared memory (buffer a; b is the
+// second buffer): P_half, then per step F, K, F^{-1}, 1/n and P (P_full between
+// steps, P_half after the last); the result is written back to S.u.
 template <typename T>
-__global__ void __launch_bounds__(kSmallThreads) small_kernel(const SmallDesc<T>* D, long long nsteps,
-                                                              int spectral) {
-  const SmallDesc<T>& S = D[blockIdx.x];
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* a = reinterpret_cast<T*>(smraw);
-  T* b = a + S.n;
+__device__ void small_steps_body(const SmallDesc<T>& S, T* a, T* b, long long nsteps) {
   const int n = S.n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = S.u[k];
-  __syncthreads();
-  if (spectral) {
-    T* c = small_dft<-1>(S, a, b);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      T x = cscale(c[k], S.inv_n);
-      S.spec[k] = make_double2((double)x.x, (double)x.y);
-    }
-    return;
-  }
-  if (nsteps <= 0) return;
   for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = apply_phase(a[k], __ldg(S.Ph + k));
   __syncthreads();
   T* cur = a;
@@ -135,6 +122,28 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const SmallDesc<T>
     __syncthreads();
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) S.u[k] = cur[k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) small_kernel(const SmallDesc<T>* D, long long nsteps,
+                                                              int spectral) {
+  const SmallDesc<T>& S = D[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* a = reinterpret_cast<T*>(smraw);
+  T* b = a + S.n;
+  const int n = S.n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = S.u[k];
+  __syncthreads();
+  if (spectral) {
+    T* c = small_dft<-1>(S, a, b);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      T x = cscale(c[k], S.inv_n);
+      S.spec[k] = make_double2((double)x.x, (double)x.y);
+    }
+    return;
+  }
+  if (nsteps <= 0) return;
+  small_steps_body(S, a, b, nsteps);
 }
 
 // --------------------------------------------------------------------------
@@ -338,8 +347,7 @@ __global__ void noalloc_tables(const double* __restrict__ v, const int32_t* __re
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double th = v[i] * turns_v;
     T a, b, c;
-    encode_phase(th, &a);
-    encode_phase(2.0 * th, &b);
+    encode_phase_pair(th, &a, &b);            // as the plan path's build_tables
     encode_phase(turns_k * (double)norm2[i], &c);
     Ph[i] = a;
     Pf[i] = b;
@@ -363,29 +371,10 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel_noalloc(const __gr
   extern __shared__ __align__(16) unsigned char smraw[];
   T* a = reinterpret_cast<T*>(smraw);
   T* b = a + S.n;
-  const int n = S.n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = S.u[k];
+  for (int k = threadIdx.x; k < S.n; k += blockDim.x) a[k] = S.u[k];
   __syncthreads();
   if (nsteps <= 0) return;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = apply_phase(a[k], S.Ph[k]);
-  __syncthreads();
-  T* cur = a;
-  for (long long step = 0; step < nsteps; ++step) {
-    T* oth = cur == a ? b : a;
-    cur = small_dft<-1>(S, cur, oth);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) cur[k] = apply_phase(cur[k], S.K[k]);
-    __syncthreads();
-    oth = cur == a ? b : a;
-    cur = small_dft<+1>(S, cur, oth);
-    const T* P = step + 1 < nsteps ? S.Pf : S.Ph;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      T x = cur[k];
-      x = cmake(fma(x.x, S.inv_n, x.x * S.inv_n_lo), fma(x.y, S.inv_n, x.y * S.inv_n_lo));
-      cur[k] = apply_phase(x, P[k]);
-    }
-    __syncthreads();
-  }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) S.u[k] = cur[k];
+  small_steps_body(S, a, b, nsteps);
 }
 
 template <typename T>
@@ -405,19 +394,7 @@ static int noalloc_run(void* scratch, long long n, double gamma, double dt, long
   S.axes[0].len = (int)n;
   S.axes[0].stride = 1;
   S.axes[0].tw_off = 0;
-  S.axes[0].nfac = 0;
-  {
-    int rem = (int)n;
-    const int pref[] = {16, 8, 4, 2};
-    for (int f : pref)
-      while (rem % f == 0 && S.axes[0].nfac < 24) { S.axes[0].fac[S.axes[0].nfac++] = f; rem /= f; }
-    for (int f = 3; f <= rem && S.axes[0].nfac < 24; f += 2)
-      while (rem % f == 0) { S.axes[0].fac[S.axes[0].nfac++] = f; rem /= f; }
-    if (rem > 1) {
-      if (S.axes[0].nfac >= 24) return LSP_ERR_TOO_LARGE;
-      S.axes[0].fac[S.axes[0].nfac++] = rem;
-    }
-  }
+  if (!factorize_axis((int)n, S.axes[0])) return LSP_ERR_TOO_LARGE;
   S.inv_n = (decltype(S.inv_n))(1.0 / (double)n);
   S.inv_n_lo = (decltype(S.inv_n))(1.0 / (double)n - (double)S.inv_n);
   const double turns_v = -dt / (4.0 * M_PI * gamma);
@@ -442,15 +419,17 @@ extern "C" int lsp_strang_steps_noalloc(int prec, int64_t n, double gamma, doubl
   // limits: the fixed scratch (8192 points) and two state copies in shared memory
   const size_t csz = prec == LSP_C64 ? sizeof(float2) : sizeof(double2);
   if (n > kNoAllocMaxN || 2 * (size_t)n * csz > (size_t)kSmallSmemBytes) return LSP_ERR_TOO_LARGE;
-  if (nsteps == 0) return LSP_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDev) return LSP_ERR_CUDA;
   if (!g_noalloc_addr[dev]) {
-    // first call on this device: device address of the file-scope scratch
+    // first call on this device (nsteps = 0 included): device address of the file-scope
+    // scratch.  With lazy module loading this also loads this file's module, which
+    // reserves the array, so the first call belongs before the allocation-free phase.
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LSP_ERR_CUDA;
     g_noalloc_addr[dev] = ptr;
   }
+  if (nsteps == 0) return LSP_OK;
   cudaStream_t s = (cudaStream_t)stream;
   return prec == LSP_C64 ? noalloc_run<float2>(g_noalloc_addr[dev], n, gamma, dt, nsteps, v, norm2, u, s)
                          : noalloc_run<double2>(g_noalloc_addr[dev], n, gamma, dt, nsteps, v, norm2, u, s);

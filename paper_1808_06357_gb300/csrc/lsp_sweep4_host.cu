@@ -251,7 +251,8 @@ int s4_class_init(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans) {
 }
 
 template <typename T>
-static int s4_class_sync_impl(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed) {
+static int s4_class_sync_impl(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed,
+                              cudaStream_t s) {
   std::vector<unsigned char> h(c.ids.size() * sizeof(S4Inst<T>));
   for (size_t k = 0; k < c.ids.size(); ++k) {
     lsp_plan p = plans[c.ids[k]];
@@ -261,18 +262,19 @@ static int s4_class_sync_impl(lsp_batch_s::S4Class& c, const std::vector<lsp_pla
   }
   *changed = h != c.inst_host;
   if (!*changed) return LSP_OK;
-  // launches of an earlier call may still read the old descriptors: let them finish first
-  if (c.inst) LSP_CUDA_TRY(cudaDeviceSynchronize());
+  // Launches of an earlier call on this stream may still read the old descriptors: the
+  // copy is ordered after them on the call's stream (a pageable-source copy returns once
+  // the source is staged, so h may go out of scope).  Not capturable into a graph.
   if (!c.inst && cudaMalloc(&c.inst, h.size()) != cudaSuccess) return LSP_ERR_OOM;
-  LSP_CUDA_TRY(cudaMemcpy(c.inst, h.data(), h.size(), cudaMemcpyHostToDevice));
+  LSP_CUDA_TRY(cudaMemcpyAsync(c.inst, h.data(), h.size(), cudaMemcpyHostToDevice, s));
   c.inst_host = h;
   return LSP_OK;
 }
 
-int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed) {
+int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, bool* changed, cudaStream_t s) {
   const int prec = plans[c.ids[0]]->prec;
-  return prec == LSP_C64 ? s4_class_sync_impl<float2>(c, plans, changed)
-                         : s4_class_sync_impl<double2>(c, plans, changed);
+  return prec == LSP_C64 ? s4_class_sync_impl<float2>(c, plans, changed, s)
+                         : s4_class_sync_impl<double2>(c, plans, changed, s);
 }
 
 template <typename T> static int s4b_launch(const void* fn, const lsp_batch_s::S4Class& c, int g, cudaStream_t s) {

@@ -5,17 +5,16 @@
   the Table 1 lattices; Strang splitting gives second order.
 * Sec. 3.3, conservation: the variation delta = (max - min) / mean of the norm and of
   the energy <H u, u> over the run (lsp_observables).
-* Sec. 3.4, initial discretisation error e_total of g1 against its exact Fourier
-  coefficients (closed form through the Faddeeva function).
+* Sec. 3.4, the lattice-rule coefficients of an initial function (the discrete side of
+  its initial discretisation error e_total; the exact coefficients are the caller's).
 
-Inputs come from the workload module (Table 1 generating vectors, g1, g2, v1, v2 at
-the lattice points the library returns); every Strang step runs in the library's
-kernels.  Errors are measured on the device in the lattice-rule L2 norm
+Inputs are passed in by the caller (a workload instance: Table 1 generating vector,
+g1 / g2 and v1 / v2 as functions of the lattice points the library returns); every
+Strang step runs in the library's kernels.  Errors are measured on the device in the lattice-rule L2 norm
 sqrt((1/n) sum |u - u_ref|^2).
 
     python -m paper_1808_06357_gb300.experiments convergence --d 2 --log2n 18 --init g1 --pot v2 --gamma 0.5
     python -m paper_1808_06357_gb300.experiments conservation --d 5 --log2n 25 --gamma 0.5
-    python -m paper_1808_06357_gb300.experiments initial_error --d 4 --log2n 25 --gamma 1
 """
 
 from __future__ import annotations
@@ -23,18 +22,13 @@ from __future__ import annotations
 import argparse
 import json
 import math
-import os
-import sys
 
 
-def _setup(d, n_log2, init, pot, gamma, prec, device=0):
+def _setup(inst, prec, device=0):
     import torch
 
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    import workloads as w
     from . import _binding as B
 
-    inst = w.paper_instance(d, n_log2, init=init, pot=pot, gamma=gamma)
     plan = B.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec, device=device)
     pts = plan.lattice_points()
     dev = torch.device("cuda", device)
@@ -42,14 +36,16 @@ def _setup(d, n_log2, init, pot, gamma, prec, device=0):
     u0 = torch.from_numpy(inst.u0(pts)).to(dev)
     del pts
     plan.set_potential(v)
-    return plan, u0, inst
+    return plan, u0
 
 
-def convergence(d=2, n_log2=18, init="g1", pot="v2", gamma=0.5, ms=(5, 10, 20, 50, 100, 200, 500, 1000),
-                M=10000, T=1.0, prec="c128", device=0):
-    """Errors ||u^M - u^m|| at time T and the observed orders between consecutive m."""
+def convergence(inst, ms=(5, 10, 20, 50, 100, 200, 500, 1000), M=10000, T=1.0, prec="c128", device=0):
+    """Errors ||u^M - u^m|| at time T and the observed orders between consecutive m.
+
+    inst: a workload instance (generating vector, n, gamma, v and u0 as functions of the
+    lattice points), e.g. workloads.paper_instance(d, log2 n, init, pot, gamma)."""
     import torch
-    plan, u0, inst = _setup(d, n_log2, init, pot, gamma, prec, device)
+    plan, u0 = _setup(inst, prec, device)
     plan.set_state(u0)
     plan.strang_steps(T / M, M)
     ref = plan.get_state(prec="c128")
@@ -68,9 +64,10 @@ def convergence(d=2, n_log2=18, init="g1", pot="v2", gamma=0.5, ms=(5, 10, 20, 5
             "errors": errs, "orders": orders}
 
 
-def conservation(d=5, n_log2=25, init="g1", pot="v2", gamma=0.5, dt=1e-3, T=1.0, every=10, prec="c128", device=0):
-    """Norm and energy every `every` steps over [0, T]; delta = (max - min) / mean of each."""
-    plan, u0, inst = _setup(d, n_log2, init, pot, gamma, prec, device)
+def conservation(inst, dt=1e-3, T=1.0, every=10, prec="c128", device=0):
+    """Norm and energy every `every` steps over [0, T]; delta = (max - min) / mean of each
+    (inst as for convergence)."""
+    plan, u0 = _setup(inst, prec, device)
     plan.set_state(u0)
     nsteps = int(round(T / dt))
     norms, energies = [], []
@@ -93,91 +90,32 @@ def conservation(d=5, n_log2=25, init="g1", pot="v2", gamma=0.5, dt=1e-3, T=1.0,
             "norm": norms, "energy": energies}
 
 
-# --------------------------------------------------------------------------
-# Sec. 3.4: the initial discretisation error of g1
-# --------------------------------------------------------------------------
-def g1_factor(h, c: float, gamma: float):
-    """I(h) = int_0^1 exp(-(2 pi x - c)^2 / gamma) exp(-2 pi i h x) dx, closed form.
+def lattice_rule_coefficients(z, n_log2, samples, gamma=1.0, prec="c128", device=0):
+    """Sec. 3.4's discrete side: the lattice-rule coefficients ghat_a(h_chi) (eq. approx_uhat)
+    of a function given by its samples at the lattice points, with the minimal-l2
+    representative h_chi of every bin.
 
-    With y = 2 pi x - c and the square completed,
-        I(h) = exp(-i h c) / (2 pi) * sqrt(pi gamma) / 2 * [E(y)]_{y=-c}^{2 pi - c},
-        E(y) = exp(-gamma h^2 / 4) erf((y + i gamma h / 2) / sqrt(gamma)),
-    and E is evaluated through the Faddeeva function w (erf z = 1 - exp(-z^2) w(i z) for
-    Re z >= 0, odd symmetry otherwise), so that no factor overflows for large h.
-    """
-    import numpy as np
-    from scipy.special import wofz
-    h = np.asarray(h, dtype=np.float64)
-    sg = math.sqrt(gamma)
-    es = np.exp(-gamma * h * h / 4.0)
-
-    def E(y):
-        z = (y + 0.5j * gamma * h) / sg
-        tail = np.exp(-y * y / gamma - 1j * h * y)             # exp(-gamma h^2 / 4 - z^2)
-        return es - tail * wofz(1j * z) if y >= 0 else -(es - tail * wofz(-1j * z))
-
-    return np.exp(-1j * h * c) / (2.0 * math.pi) * (math.sqrt(math.pi * gamma) / 2.0) * (E(2 * math.pi - c) - E(-c))
-
-
-def g1_norm_factor(c: float, gamma: float) -> float:
-    """int_0^1 exp(-2 (2 pi x - c)^2 / gamma) dx (one factor of ||g1||^2 before normalisation)."""
-    from scipy.special import erf
-    a = math.sqrt(2.0 / gamma)
-    return (1.0 / (2.0 * math.pi)) * math.sqrt(math.pi * gamma / 2.0) / 2.0 * (erf(a * (2 * math.pi - c)) - erf(-a * c))
-
-
-def g1_centres(d: int):
-    return [1.5 * math.pi] + [math.pi] * (d - 1)
-
-
-def g1_coefficients(H, gamma: float):
-    """Exact Fourier coefficients ghat(h) of g1 with unit L2 norm on [0,1)^d, for the rows h of H."""
-    import numpy as np
-    H = np.asarray(H)
-    d = H.shape[1]
-    cs = g1_centres(d)
-    norm2 = 1.0
-    for c in cs:
-        norm2 *= g1_norm_factor(c, gamma)
-    out = np.full(H.shape[0], 1.0 / math.sqrt(norm2), dtype=np.complex128)
-    for j in range(d):
-        lo, hi = int(H[:, j].min()), int(H[:, j].max())
-        tab = g1_factor(np.arange(lo, hi + 1), cs[j], gamma)
-        out *= tab[H[:, j] - lo]
-    return out
-
-
-def initial_error(d=2, n_log2=18, gamma=1.0, prec="c128", device=0):
-    """e_total = ||g1 - g1_a||_L2 (Sec. 3.4): with ||g1|| = 1,
-    e_total^2 = 1 - sum_{h in A} |ghat(h)|^2 + sum_{h in A} |ghat(h) - ghat_a(h)|^2,
-    ghat exact (g1_coefficients), ghat_a the lattice-rule coefficients computed by the library."""
+    samples: a callable mapping the (n, d) lattice points to the n complex samples.
+    Returns (ghat_a, H): ghat_a in bin order (numpy complex128) and H (n, d) int32.
+    e_total = ||g - g_a|| then follows from the exact coefficients of g:
+    e_total^2 = ||g||^2 - sum_{h in A} |ghat(h)|^2 + sum_{h in A} |ghat(h) - ghat_a(h)|^2."""
     import numpy as np
     import torch
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    import workloads as w
     from . import _binding as B
-    z = w.table1_z(d, n_log2)
     plan = B.Plan(z, (1 << n_log2,), gamma, prec=prec, device=device)
     pts = plan.lattice_points()
-    cs = np.array(g1_centres(d))
-    shape = np.exp(-np.sum((2.0 * np.pi * pts - cs) ** 2, axis=1) / gamma)
+    u = np.asarray(samples(pts), dtype=np.complex128)
     del pts
-    norm2 = 1.0
-    for c in cs:
-        norm2 *= g1_norm_factor(float(c), gamma)
-    plan.set_state(torch.from_numpy((shape / math.sqrt(norm2)).astype(np.complex128)).to(torch.device("cuda", device)))
+    plan.set_state(torch.from_numpy(u).to(torch.device("cuda", device)))
     ga = plan.get_state(space="spectral", prec="c128").cpu().numpy()
-    g = g1_coefficients(plan.index_table(), gamma)
-    inside = float(np.sum(np.abs(g) ** 2))
-    alias = float(np.sum(np.abs(g - ga) ** 2))
-    e2 = max(0.0, 1.0 - inside) + alias
-    return {"experiment": "initial_error", "d": d, "n": 1 << n_log2, "gamma": gamma, "prec": prec,
-            "outside_A": max(0.0, 1.0 - inside), "aliasing": alias, "e_total": math.sqrt(e2)}
+    H = plan.index_table()
+    plan.destroy()
+    return ga, H
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("experiment", choices=["convergence", "conservation", "initial_error"])
+    ap.add_argument("experiment", choices=["convergence", "conservation"])
     ap.add_argument("--d", type=int, default=2)
     ap.add_argument("--log2n", type=int, default=18)
     ap.add_argument("--init", default="g1", choices=["g1", "g2"])
@@ -190,12 +128,15 @@ def main(argv=None):
     ap.add_argument("--T", type=float, default=1.0)
     ap.add_argument("--every", type=int, default=10)
     a = ap.parse_args(argv)
+    try:
+        import workloads as w
+    except ImportError as e:
+        raise SystemExit("run from the repository root: the input generators (workloads/) are needed") from e
+    inst = w.paper_instance(a.d, a.log2n, init=a.init, pot=a.pot, gamma=a.gamma)
     if a.experiment == "convergence":
-        r = convergence(a.d, a.log2n, a.init, a.pot, a.gamma, tuple(int(x) for x in a.ms.split(",")), a.M, a.T, a.prec)
-    elif a.experiment == "initial_error":
-        r = initial_error(a.d, a.log2n, a.gamma, a.prec)
+        r = convergence(inst, tuple(int(x) for x in a.ms.split(",")), a.M, a.T, a.prec)
     else:
-        r = conservation(a.d, a.log2n, a.init, a.pot, a.gamma, a.dt, a.T, a.every, a.prec)
+        r = conservation(inst, a.dt, a.T, a.every, a.prec)
         r = {k: v for k, v in r.items() if k not in ("norm", "energy")}
     print(json.dumps(r))
 

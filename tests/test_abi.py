@@ -88,3 +88,20 @@ def test_cbc_argument_checks_without_gpu():
         with pytest.raises(lsp.LspError) as e:
             lsp.cbc_reconstructing(I, 8, cand)
         assert e.value.code == -6
+
+
+def test_noalloc_binding_refuses_unchecked_buffers():
+    """The allocation-free entry point takes raw pointers: the binding refuses host
+    arrays, wrong dtypes and short buffers before any call reaches the library."""
+    import numpy as np
+    import pytest
+    import torch
+    import paper_1808_06357_gb300 as lsp
+    u = np.zeros(16, dtype=np.complex64)
+    v = np.zeros(16)
+    nrm = np.zeros(16, dtype=np.int32)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        lsp.strang_steps_noalloc(u, v, nrm, 0.1, 1e-3, 1)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        lsp.strang_steps_noalloc(torch.zeros(16, dtype=torch.complex64), torch.zeros(16, dtype=torch.float64),
+                                 torch.zeros(16, dtype=torch.int32), 0.1, 1e-3, 1)

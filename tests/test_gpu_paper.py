@@ -79,8 +79,8 @@ def test_convergence_protocol_matches_oracle(lib):
     in this range.)"""
     from paper_1808_06357_gb300 import experiments as X
     ms = (10, 20, 40, 80)
-    r = X.convergence(d=2, n_log2=18, init="g1", pot="v1", gamma=0.5, ms=ms, M=1000, T=0.2, prec="c128")
     inst = w.paper_instance(2, 18, init="g1", pot="v1", gamma=0.5)
+    r = X.convergence(inst, ms=ms, M=1000, T=0.2, prec="c128")
     P, norms, v, u0 = _oracle_setup(inst)
     ref = S.strang(u0, v, norms, inst.n, inst.gamma, 0.2 / 1000, 1000)
     for m in ms:
@@ -95,8 +95,8 @@ def test_conservation_matches_oracle(lib):
     """Sec. 3.3 observables along a run (d = 2, n = 2^18, g1, v2, gamma = 0.5): the GPU's norm and
     energy at every sample equal the oracle's; the norm varies at round-off only."""
     from paper_1808_06357_gb300 import experiments as X
-    r = X.conservation(d=2, n_log2=18, init="g1", pot="v2", gamma=0.5, dt=1e-2, T=0.5, every=5, prec="c128")
     inst = w.paper_instance(2, 18, init="g1", pot="v2", gamma=0.5)
+    r = X.conservation(inst, dt=1e-2, T=0.5, every=5, prec="c128")
     P, norms, v, u0 = _oracle_setup(inst)
     Ph = S.potential_half_phase(v, inst.gamma, 1e-2)
     K = S.kinetic_phase(norms, inst.gamma, 1e-2)
@@ -139,25 +139,24 @@ def test_table1_high_dimension_full_size(lib):
 
 def test_initial_error_matches_oracle_coefficients(lib):
     """Sec. 3.4 e_total of g1 (gamma = 1) on the d = 2 Table 1 lattices: the library's lattice-rule
-    coefficients give the same e_total as the oracle's, and it falls from n = 2^18 to 2^20."""
-    import math
+    coefficients equal the oracle's, so both give the same e_total against the exact coefficients,
+    and e_total falls from n = 2^18 to 2^20."""
+    from oracle import initial_error as G
     from paper_1808_06357_gb300 import experiments as X
-    r18 = X.initial_error(d=2, n_log2=18, gamma=1.0)
-    r20 = X.initial_error(d=2, n_log2=20, gamma=1.0)
-    z = w.table1_z(2, 18)
-    n = (1 << 18,)
-    P = L.lattice_points(z, n)
-    cs = np.array(X.g1_centres(2))
-    norm2 = X.g1_norm_factor(cs[0], 1.0) * X.g1_norm_factor(cs[1], 1.0)
-    u = np.exp(-np.sum((2 * np.pi * P - cs) ** 2, axis=1)) / math.sqrt(norm2)
-    ga = S.coeffs(u, n)
-    _, B = L.minl2_norms_dp(z, n)
-    H = lib.Plan(z, n, 1.0, prec="c128").index_table()
-    assert np.array_equal(L.chi_index(H, z, n), np.arange(n[0]))
-    g = X.g1_coefficients(H, 1.0)
-    e = math.sqrt(max(0.0, 1 - np.sum(np.abs(g) ** 2)) + np.sum(np.abs(g - ga) ** 2))
-    assert abs(r18["e_total"] - e) < 1e-9 * e
-    assert r20["e_total"] < r18["e_total"]
+    es = {}
+    for lg in (18, 20):
+        z = w.table1_z(2, lg)
+        ga, H = X.lattice_rule_coefficients(z, lg, lambda p: G.g1_samples(p, 1.0), gamma=1.0)
+        n = (1 << lg,)
+        assert np.array_equal(L.chi_index(H, z, n), np.arange(n[0]))
+        g = G.g1_coefficients(H, 1.0)
+        es[lg] = G.e_total(g, ga)
+        if lg == 18:
+            P = L.lattice_points(z, n)
+            ref = S.coeffs(G.g1_samples(P, 1.0), n)
+            assert np.max(np.abs(ga - ref)) < 1e-12
+            assert abs(es[lg] - G.e_total(g, ref)) < 1e-9 * es[lg]
+    assert es[20] < es[18]
 
 
 @pytest.mark.parametrize("which", ["smem", "two-sweep", "four-sweep", "rank-2"])

@@ -1,11 +1,11 @@
-"""Closed-form Fourier coefficients of the paper's g1 (Sec. 3.4) against quadrature (no GPU)."""
+"""Pins of the oracle's closed-form Fourier coefficients of g1 (Sec. 3.4): quadrature and Parseval (no GPU)."""
 
 import math
 
 import numpy as np
 import pytest
 
-from paper_1808_06357_gb300 import experiments as X
+from oracle import initial_error as X
 
 
 def _quad(h, c, gamma, m=200000):
