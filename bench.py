@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-plan", action="store_true", help="skip the plan-time (DP, CBC) side measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--no-rank2", action="store_true", help="skip the rank-2 2^14 x 2^12 batch measurement")
+    ap.add_argument("--no-side", action="store_true", help="skip the C1, C4 and rank-1 2^24 side measurements")
     ap.add_argument("--log2n", type=int, default=22, help="lattice size 2^m of the d=6 workload (profiling)")
     ap.add_argument("--inner", type=int, default=STEPS_PER_CALL, help="Strang steps per bench step")
     ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
@@ -59,6 +60,7 @@ KERNEL_SOURCES = {
     "mp_persistent": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_mp.cuh", "lsp_mp_c64_hi.cu"],
     "sweep4_rank2": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_sweep4.cuh", "lsp_sweep4_r2.cu"],
     "sweep4_rank1": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_sweep4.cuh", "lsp_sweep4_r1.cu"],
+    "s2": ["lsp_internal.cuh", "lsp_tile.cuh", "lsp_async.cuh", "lsp_s2.cuh", "lsp_s2.cu"],
 }
 
 
@@ -181,23 +183,82 @@ def c2_inputs(m: int = 22):
     return w.c2(m)
 
 
+def host_description():
+    """CPU model and core count of this host (recorded with every oracle timing)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"cpu": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
+
+
+def _oracle_worker(args):
+    """One oracle replica (spawned process): FP64 Strang steps on the full state for ~budget_s."""
+    m, budget_s = args
+    import workloads as w
+    from oracle import lattice as L
+    from oracle import strang as S
+    inst = w.c2(m)
+    P = L.lattice_points(inst.Z, inst.n)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    v, u0 = inst.v(P), inst.u0(P)
+    del P
+    S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 1)            # warm
+    steps, t0, u = 0, time.perf_counter(), u0
+    while time.perf_counter() - t0 < budget_s:
+        u = S.strang(u, v, norms, inst.n, inst.gamma, inst.dt, 1)
+        steps += 1
+    return steps, time.perf_counter() - t0
+
+
 def cpu_oracle_rate(inst, budget_s: float = 15.0):
-    """The FP64 oracle (as it stands) on a bounded sample: a few Strang steps on the full state."""
+    """The FP64 oracle (as it stands) on a bounded sample: Strang steps on the full state, first on
+    one core, then as independent replicas on every host core (spawned processes; numpy's FFT
+    is single-threaded, so replicas are how the oracle uses all cores)."""
     import numpy as np
     from oracle import lattice as L
     from oracle import strang as S
     P = L.lattice_points(inst.Z, inst.n)
     norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
     v, u0 = inst.v(P), inst.u0(P)
+    del P
     S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 1)          # warm
     steps, t0 = 0, time.perf_counter()
     u = u0
-    chunk = 2
-    while time.perf_counter() - t0 < budget_s:
-        u = S.strang(u, v, norms, inst.n, inst.gamma, inst.dt, chunk)
-        steps += chunk
+    while time.perf_counter() - t0 < budget_s / 2:
+        u = S.strang(u, v, norms, inst.n, inst.gamma, inst.dt, 1)
+        steps += 1
     el = time.perf_counter() - t0
-    return inst.npoints * steps / el, steps, el
+    one = {"value": inst.npoints * steps / el, "steps": steps, "seconds": el}
+    del u, v, u0
+    cores = os.cpu_count() or 1
+    m = int(round(math.log2(inst.npoints)))
+    import multiprocessing as mp
+    try:
+        with mp.get_context("spawn").Pool(processes=cores) as pool:
+            res = pool.map(_oracle_worker, [(m, budget_s / 2)] * cores)
+        tot = sum(inst.npoints * st / sec for st, sec in res)
+        allc = {"value": tot, "replicas": cores, "steps_per_replica": [st for st, _ in res]}
+    except Exception as e:                                           # e.g. not enough host memory
+        allc = {"value": None, "error": str(e)[:200]}
+    return one, allc
 
 
 def run_reference(args):
@@ -230,7 +291,8 @@ def run_reference(args):
         "config": {"workload": "rank-1 lattice d=6 n=2^22 HC(64) reconstructing, MINL2, gamma=0.05, dt=1e-3",
                    "strang_steps_per_bench_step": per_step, "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": "lattice-point steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} Strang steps of the full n=2^22 state per bench step"},
+                         "sample": f"{per_step} Strang steps of the full n=2^22 state per bench step",
+                         "host": host_description()},
         "e2e": {"value": value, "unit": "lattice-point steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -356,11 +418,27 @@ def run_ours(args):
                   "alg_bytes_per_launch": k_bytes, "sweep_ms": sw}
         achieved = k_bytes / (sw["K"] / 1e3) / 1e9
         traffic = k_traffic
+    elif path == lsp.PATH_RANK1_TMA:
+        # two sweeps per step, each 24 algorithmic bytes per point (state read and written, one
+        # phase table: P in the column sweep, K in the row sweep); the slower one is reported
+        sw = plan.sweep_times(inst.dt, 64, stream=stream)
+        k_bytes = 24.0 * n
+        which = "P" if sw["P"] >= sw["K"] else "K"
+        name = ("s2 column sweep (conj W_n, IDFT_N2, 1/n, P, DFT_N2, W_n; TMA tensor tiles)" if which == "P" else
+                "s2 row sweep (DFT_4096, K by byte index, IDFT_4096; TMA bulk tiles)")
+        rec = traffic_record(f"c64_n2p{args.log2n}_tma", "s2") if STEPS_PER_CALL == 1000 else None
+        k_traffic = rec.get("per_launch", {}).get(which) if rec else None
+        step_traffic = rec.get("bytes_per_call_1000_steps") if rec else None
+        kernel = {"name": name, "ms_per_launch": sw[which], "alg_bytes_per_launch": k_bytes,
+                  "sweep_ms": {"column": sw["P"], "row": sw["K"]}}
+        achieved = k_bytes / (sw[which] / 1e3) / 1e9
+        traffic = k_traffic
     else:
         kernel = {"name": "mp_persistent (all 2N-1 sweeps of a call in one launch)",
                   "ms_per_launch": statistics.mean(ms), "alg_bytes_per_launch": alg_bytes}
         achieved, traffic = step_achieved, step_traffic
-    launches = {lsp.PATH_MULTIPASS: 5, lsp.PATH_RANK1_4SWEEP: 3 + 4 * STEPS_PER_CALL}.get(path, 0)
+    launches = {lsp.PATH_MULTIPASS: 5, lsp.PATH_RANK1_4SWEEP: 3 + 4 * STEPS_PER_CALL,
+                lsp.PATH_RANK1_TMA: 3 + 2 * STEPS_PER_CALL}.get(path, 0)
 
     # complex128 side measurement on the same workload
     c128 = None
@@ -379,8 +457,15 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         t2 = e0.elapsed_time(e1) / 1e3
+        fp64 = lsp.fma_rate("c128", device=local)
+        flops = 10.0 * math.log2(n) + 12.0                 # algorithmic flops per point-step (two FFTs, two phases)
+        tf = flops * n * steps2 / t2 / 1e12
         c128 = {"value": n * steps2 / t2, "unit": "lattice-point steps/s", "steps_timed": steps2,
-                "achieved_GBps": 96.0 * n * steps2 / t2 / 1e9}
+                "path": p2.info()["path"], "achieved_GBps": 96.0 * n * steps2 / t2 / 1e9,
+                "roofline": {"bound": "alu", "achieved": tf, "peak": fp64, "unit": "TFLOP/s", "frac": tf / fp64,
+                             "peak_source": "measured: lsp_fma_rate (FP64 FMA chains on every SM, CUDA events)",
+                             "flops_per_point_step": flops,
+                             "hbm_frac": 96.0 * n * steps2 / t2 / 1e9 / peaks()[0]}}
         p2.destroy()
 
     # end-to-end through the public API with host buffers (pinned), per bench step:
@@ -415,12 +500,26 @@ def run_ours(args):
     plan_time = None
     if rank == 0 and not args.no_plan:
         plan_time = measure_plan_time(lsp, inst, local)
+    side = None
+    if not args.no_side and args.log2n == 22:
+        side = {"c1": measure_c1(lsp, torch, dev, local, stream, world),
+                "c4_adjoint": measure_c4(lsp, torch, dev, local, flush, stream, world),
+                "rank1_2p24": measure_large(lsp, torch, dev, local, flush, stream, world, 24)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, steps, el = cpu_oracle_rate(inst)
-        cpu = {"value": rate, "unit": "lattice-point steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{steps} FP64 Strang steps of the full n=2^22 state ({el:.1f} s, numpy FFT, 1 thread)"}
+        one, allc = cpu_oracle_rate(inst)
+        host = host_description()
+        if allc.get("value"):
+            cpu = {"value": allc["value"], "unit": "lattice-point steps/s", "cores": allc["replicas"], "kind": "oracle",
+                   "sample": f"FP64 Strang steps of the full n=2^22 state for ~7.5 s in each of {allc['replicas']} "
+                             f"independent replicas (spawned processes, numpy FFT, 1 thread each)",
+                   "single_core": {"value": one["value"], "sample": f"{one['steps']} steps in {one['seconds']:.1f} s"},
+                   "host": host}
+        else:
+            cpu = {"value": one["value"], "unit": "lattice-point steps/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{one['steps']} FP64 Strang steps of the full n=2^22 state ({one['seconds']:.1f} s, "
+                             f"numpy FFT, 1 thread)", "all_cores_error": allc.get("error"), "host": host}
         if plan_time is not None:
             cpu["plan_time"] = cbc_oracle_time(plan_time)
 
@@ -435,7 +534,8 @@ def run_ours(args):
                                    "complex64 state", "l2": "flushed (512 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}",
                        "path": {0: "two-sweep persistent (4096 x 1024)",
-                                3: "four-sweep (4096 x 32 x 32)"}.get(path, str(path)),
+                                3: "four-sweep (4096 x 32 x 32)",
+                                4: "two-sweep, TMA-fed tiles (4096 x 1024)"}.get(path, str(path)),
                        "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
                        "autotune_steps": min(100, STEPS_PER_CALL)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -447,6 +547,7 @@ def run_ours(args):
             "batched": batched,
             "rank2": rank2,
             "plan_time": plan_time,
+            "side": side,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
@@ -457,6 +558,112 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _event_ms(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_c1(lsp, torch, dev, local, stream, world):
+    """C1: d = 2, n = 961 = 31^2, z = (1, 31), box |h_j| <= 15 (explicit set), gamma = 0.1, dt = 1e-3,
+    1000 steps per call on the SMEM-resident path (one CTA runs every step), complex128 and complex64."""
+    import numpy as np
+    import workloads as w
+    inst = w.c1()
+    out = {"workload": "rank-1 lattice d=2 n=961 z=(1,31), explicit box |h_j|<=15, gamma=0.1, dt=1e-3, "
+                       "1000 steps per call; the 15 KB state stays in one SM's shared memory"}
+    for prec in ("c128", "c64"):
+        p = lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec, aa="explicit", index_set=inst.index_set, device=local)
+        pts = p.lattice_points()
+        p.set_potential(torch.from_numpy(inst.v(pts)).to(dev))
+        u0 = torch.from_numpy(inst.u0(pts)).to(dev)
+        p.set_state(u0)
+        p.strang_steps(inst.dt, 1000)
+        torch.cuda.synchronize()
+        ms = [_event_ms(torch, stream, lambda: p.strang_steps(inst.dt, 1000)) for _ in range(3)]
+        t = max_over_ranks(sum(ms), world) / 1e3
+        out[prec] = {"value": world * inst.npoints * 1000 * len(ms) / t, "unit": "lattice-point steps/s",
+                     "ms_per_call": 1e3 * t / len(ms), "path": p.info()["path"]}
+        p.destroy()
+    return out
+
+
+def measure_c4(lsp, torch, dev, local, flush, stream, world):
+    """C4: the adjoint call (d = 4, n = 2^20, 500 steps, ceil(sqrt(500)) checkpoints, complex64):
+    forward run with checkpoints, recomputation per segment, backward run and gradient
+    accumulation; reported as gradients per second and as lattice-point steps per second of
+    the forward run they cover."""
+    import numpy as np
+    import workloads as w
+    inst = w.c4(20)
+    p = lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64", device=local)
+    pts = p.lattice_points()
+    v = torch.from_numpy(inst.v(pts)).to(dev)
+    u0 = torch.from_numpy(inst.u0(pts).astype(np.complex64)).to(dev)
+    phi = torch.from_numpy(inst.phi(pts)).to(dev)
+    del pts
+    p.set_potential(v)
+    lam = (2.0 * phi / inst.npoints).to(torch.complex64)
+    gv = torch.empty(inst.npoints, dtype=torch.float64, device=dev)
+    gu = torch.empty(inst.npoints, dtype=torch.complex64, device=dev)
+
+    def call():
+        p.set_state(u0)
+        lsp.adjoint(p, inst.dt, inst.nsteps, lam, gv, gu, 0)
+    call()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(2):
+        flush.fill_(1.0)
+        ms.append(_event_ms(torch, stream, call))
+    if p.status() != 0:
+        raise RuntimeError("adjoint status " + lsp.strerror(p.status()))
+    t = max_over_ranks(sum(ms), world) / 1e3
+    out = {"value": world * len(ms) / t, "unit": "gradients/s", "ms_per_gradient": 1e3 * t / len(ms),
+           "forward_equivalent": world * inst.npoints * inst.nsteps * len(ms) / t, "path": p.info()["path"],
+           "workload": "d=4 n=2^20 random-unit rank-1 lattice, MINL2 set, gamma=0.1, dt=1e-3, 500 steps, grad of "
+                       "|<u_T, phi>|^2 wrt v and u0, ceil(sqrt(500)) checkpoints, complex64"}
+    p.destroy()
+    return out
+
+
+def measure_large(lsp, torch, dev, local, flush, stream, world, m):
+    """Rank-1 n = 2^m beyond L2 (2^24 complex64: 128 MiB state, 128 MiB of each phase table), d = 6,
+    100 steps per call on every available path (after one untimed call each); the fastest path's
+    rate against the method's 48 B per point-step."""
+    import numpy as np
+    import workloads as w
+    inst = w.c2(m)
+    p = lsp.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64", device=local)
+    pts = p.lattice_points()
+    p.set_potential(torch.from_numpy(inst.v(pts)).to(dev))
+    u0 = torch.from_numpy(inst.u0(pts).astype(np.complex64)).to(dev)
+    del pts
+    hbm, _ = peaks()
+    per_path = {}
+    for path in p.paths():
+        p.set_path(path)
+        p.set_state(u0)
+        p.strang_steps(inst.dt, 100)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        t = _event_ms(torch, stream, lambda: p.strang_steps(inst.dt, 100)) / 1e3
+        per_path[path] = inst.npoints * 100 / t
+    if p.status() != 0:
+        raise RuntimeError("status " + lsp.strerror(p.status()))
+    best = max(per_path, key=per_path.get)
+    rate = per_path[best]
+    p.destroy()
+    return {"value": world * rate, "unit": "lattice-point steps/s", "path": best,
+            "per_path": {str(k): v for k, v in per_path.items()},
+            "roofline": {"bound": "hbm", "achieved": 48.0 * rate / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": 48.0 * rate / 1e9 / hbm, "alg_bytes_per_point_step": 48},
+            "workload": f"rank-1 lattice d=6 n=2^{m} random units, MINL2 set, gamma=0.05, dt=1e-3, 100 steps per call"}
 
 
 def measure_plan_time(lsp, inst, local):

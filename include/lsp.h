@@ -87,7 +87,7 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
- * 0, 3, 1, but for complex64 1, 3, 0 at n = 2^13 and 3, 0, 1 from n = 2^20;
+ * 0, 3, 1, 4, but for complex64 1, 3, 0, 4 at n = 2^13 and 3, 0, 1, 4 from n = 2^20;
  * rank 2: 1, 2; reported by lsp_plan_info, changed by lsp_plan_set_path or
  * lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
@@ -96,7 +96,8 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *     state stays in registers across the steps, one line FFT per step);
  *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
  *     (10, 8), (11, 9), (12, 10), (14, 12);
- *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25}.
+ *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25};
+ *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 20 <= m <= 23.
  * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
@@ -205,7 +206,8 @@ enum {
   LSP_PATH_MULTIPASS = 0,      /* rank-1, n = 2^m: two sweeps per step (persistent kernel)        */
   LSP_PATH_SMEM = 1,           /* whole run in shared memory, one CTA per instance                 */
   LSP_PATH_RANK2 = 2,          /* rank-2, 2^m1 x 2^m2: four sweeps per step                        */
-  LSP_PATH_RANK1_4SWEEP = 3    /* rank-1, n = 2^m: four sweeps per step (rows of 4096 points)      */
+  LSP_PATH_RANK1_4SWEEP = 3,   /* rank-1, n = 2^m: four sweeps per step (rows of 4096 points)      */
+  LSP_PATH_RANK1_TMA = 4       /* rank-1, n = 2^m: two sweeps per step, tiles brought in by TMA    */
 };
 
 /*
@@ -230,7 +232,7 @@ int lsp_plan_set_path(lsp_plan p, int path);
  * copy of the state (the plan's state is not changed), and keep the fastest.
  * Not in the paper: a schedule choice.
  *   chosen  receives the kept path (may be NULL).
- *   ms      NULL, or 4 doubles receiving each path's time in ms (-1: not available).
+ *   ms      NULL, or 5 doubles receiving each path's time in ms (-1: not available).
  * Synchronises `stream`.  Errors: BAD_ARG, OOM, CUDA, TIMEOUT (then the plan
  * keeps the path it had).
  */
@@ -341,12 +343,13 @@ int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r, const int6
                            int64_t ncand, int64_t* Z_out, int* fixed, int device);
 
 /*
- * lsp_sweep_times -- per-sweep durations of the four-sweep paths (2 and 3):
+ * lsp_sweep_times -- per-sweep durations of the multi-launch paths (2, 3, 4):
  * nsteps (2 .. 4096) Strang steps of size dt on a scratch copy of the state,
  * once untimed, then again as plain launches with a CUDA event after each;
  * ms[0..3] (host) = mean duration in ms of the P sweep between steps (rows /
- * X), the A / Y sweep, the K sweep (B / Z) and the A^-1 / Y^-1 sweep.  The
- * plan's state is unchanged; its phase tables are rebuilt for dt.
+ * X / the column sweep of path 4), the A / Y sweep, the K sweep (B / Z / the
+ * row sweep of path 4) and the A^-1 / Y^-1 sweep (-1 where a path has none).
+ * The plan's state is unchanged; its phase tables are rebuilt for dt.
  * Synchronous.  Errors: BAD_ARG, UNSUPPORTED (other paths), OOM, CUDA, TIMEOUT.
  */
 int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double* ms);

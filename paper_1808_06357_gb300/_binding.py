@@ -19,7 +19,8 @@ LSP_OK = 0
 C64, C128 = 1, 2
 AA_MINL2, AA_EXPLICIT = 0, 1
 PHYSICAL, SPECTRAL = 0, 1
-PATH_MULTIPASS, PATH_SMALL, PATH_RANK2, PATH_RANK1_4SWEEP = 0, 1, 2, 3
+PATH_MULTIPASS, PATH_SMALL, PATH_RANK2, PATH_RANK1_4SWEEP, PATH_RANK1_TMA = 0, 1, 2, 3, 4
+NUM_PATHS = 5
 
 _lib = None
 _lock = threading.Lock()
@@ -263,13 +264,14 @@ class Plan:
         """Execution paths this plan can run (lsp_plan_paths)."""
         m = C.c_int()
         _check(self._lib.lsp_plan_paths(self._h, C.byref(m)), "lsp_plan_paths")
-        return [k for k in range(4) if m.value >> k & 1]
+        return [k for k in range(NUM_PATHS) if m.value >> k & 1]
 
     def set_path(self, path: int):
         _check(self._lib.lsp_plan_set_path(self._h, int(path)), "lsp_plan_set_path")
 
     def sweep_times(self, dt: float, nsteps: int, stream=None) -> dict:
-        """lsp_sweep_times: mean ms per launch of the P, A / Y, K and A^-1 / Y^-1 sweeps (four-sweep paths)."""
+        """lsp_sweep_times: mean ms per launch of the P, A / Y, K and A^-1 / Y^-1 sweeps (multi-launch
+        paths; the TMA two-sweep path has only the P (column) and K (row) sweeps, the others are -1)."""
         ms = np.zeros(4, dtype=np.float64)
         _check(self._lib.lsp_sweep_times(self.handle, float(dt), int(nsteps), _stream_ptr(stream),
                                          C.c_void_p(ms.ctypes.data)), "lsp_sweep_times")
@@ -278,10 +280,10 @@ class Plan:
     def autotune(self, dt: float, nsteps: int, stream=None):
         """Time nsteps steps on every available path, keep the fastest; returns (path, {path: ms})."""
         chosen = C.c_int()
-        ms = (C.c_double * 4)()
+        ms = (C.c_double * NUM_PATHS)()
         _check(self._lib.lsp_plan_autotune(self._h, float(dt), int(nsteps), _stream_ptr(stream), C.byref(chosen), ms),
                "lsp_plan_autotune")
-        return chosen.value, {k: ms[k] for k in range(4) if ms[k] >= 0}
+        return chosen.value, {k: ms[k] for k in range(NUM_PATHS) if ms[k] >= 0}
 
     def info(self) -> dict:
         x = np.zeros(8, dtype=np.int64)

@@ -151,7 +151,7 @@ __global__ void build_klut(T* lut, int count, double turns_k) {
 
 // Bin chi held at position i of the K sweep's native order (identity for the SMEM path).
 __device__ __forceinline__ long long native_bin(long long i, int order, int logN1, int logN2) {
-  if (order == kPathMultipass) {                     // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
+  if (order == kPathMultipass || order == kPathRank1x2) {   // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
     long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
     return xi2 + (xi1 << logN2);
   }
@@ -193,10 +193,18 @@ __global__ void build_tables(const double* __restrict__ v, const int32_t* __rest
 }
 
 // ||h||^2 of the bin at each native position, as a byte (four-sweep paths, max ||h||^2 < 256).
+// TMA two-sweep path: thread-major within each row of N1 = 4096 positions, so that a thread's
+// 16 bytes are adjacent: position 16 j + q of row xi2 holds xi1 = j + 256 q.
 __global__ void build_kidx(const int32_t* __restrict__ norm2, uint8_t* kidx, long long n, int order, int logN1,
                            int logN2) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    kidx[i] = (uint8_t)norm2[native_bin(i, order, logN1, logN2)];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long pos = i;
+    if (order == kPathRank1x2) {
+      const long long row = i >> logN1, w = i & ((1ll << logN1) - 1);
+      pos = (row << logN1) + (w >> 4) + ((w & 15) << (logN1 - 4));
+    }
+    kidx[i] = (uint8_t)norm2[native_bin(pos, order, logN1, logN2)];
+  }
 }
 
 template <typename S, typename D> __device__ __forceinline__ D cvt(S x);
@@ -356,7 +364,7 @@ static void free_plan(lsp_plan p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   void* bufs[] = {p->u, p->v, p->norm2, p->Ph, p->Pf, p->K, p->klut, p->kidx, p->tw_line, p->tw_fine,
-                  p->tw_coarse, p->tw_pass, p->tw_small, p->stage, p->work, p->desc, p->bar, p->err};
+                  p->tw_coarse, p->tw_pass, p->tw_small, p->stage, p->work, p->desc, p->s2desc, p->bar, p->err};
   for (void* b : bufs) if (b) cudaFree(b);
   if (p->err_host) cudaFreeHost(p->err_host);
   if (p->s4_graph) cudaGraphExecDestroy(p->s4_graph);
@@ -393,6 +401,7 @@ static bool path_available(lsp_plan p, int path) {
     case kPathSmall: return 2 * (size_t)p->ntot * sz <= (size_t)kSmallSmemBytes;
     case kPathMultipass: return p->r == 1 && logn >= 13 && multipass_supports(p->prec, logn);
     case kPathRank1x4: return p->r == 1 && logn > 0 && s4_supports_rank1(p->prec, logn);
+    case kPathRank1x2: return p->r == 1 && logn > 0 && s2_supports(p->prec, logn);
     case kPathRank2: {
       const int m1 = ilog2exact(p->n[0]), m2 = ilog2exact(p->n[1]);
       return p->r == 2 && m1 > 0 && m2 > 0 && s4_supports_rank2(p->prec, m1, m2);
@@ -444,6 +453,24 @@ static int setup_path_tables(lsp_plan p, int path) {
     passes(tw, p->logN2);
     if ((rc = upload(p, &p->tw_pass, tw))) return rc;
     return multipass_upload_desc(p, 0);
+  }
+  if (path == kPathRank1x2) {
+    // rows of N1 = 4096 points, columns of N2 = n / 4096 (TMA-fed two-sweep kernels)
+    p->logN1 = 12;
+    p->logN2 = logn - 12;
+    p->N1 = 1 << p->logN1; p->N2 = 1 << p->logN2;
+    p->logLmax = 12;
+    twid(tw, 1ll << p->logN1, 1ll << p->logN1);              // W_N1^k
+    if ((rc = upload(p, &p->tw_coarse, tw))) return rc;
+    tw.clear();
+    twid(tw, 1ll << p->logN2, ntot);                         // W_n^k, k < N2
+    if ((rc = upload(p, &p->tw_fine, tw))) return rc;
+    tw.clear();
+    passes(tw, p->logN1);
+    p->twr_entries = (int)(tw.size() / sz);
+    passes(tw, p->logN2);
+    if ((rc = upload(p, &p->tw_pass, tw))) return rc;
+    return s2_upload_desc(p);
   }
   if (path == kPathRank1x4 || path == kPathRank2) {
     int rows, cols;                                  // log2 of the row length and of the strided axis
@@ -511,17 +538,19 @@ static int setup_path_tables(lsp_plan p, int path) {
 // The byte index of K for the four-sweep paths (when every ||h||^2 fits in a byte and the
 // norms are known); otherwise the paths read the K table.
 static int setup_kidx(lsp_plan p) {
-  const bool want = (p->path == kPathRank2 || p->path == kPathRank1x4) && p->klut && p->max_norm2 < kKIdxMax;
+  const bool want = (p->path == kPathRank2 || p->path == kPathRank1x4 || p->path == kPathRank1x2) && p->klut &&
+                    p->max_norm2 < kKIdxMax;
   if (!want) {
     if (p->kidx) { cudaFree(p->kidx); p->kidx = nullptr; }
-    return LSP_OK;
+    return p->path == kPathRank1x2 ? s2_upload_desc(p) : LSP_OK;
   }
   if (!p->kidx) {
     int rc = dalloc(p, &p->kidx, (size_t)p->ntot);
     if (rc) return rc;
   }
   build_kidx<<<grid_for(p->ntot), 256>>>(p->norm2, p->kidx, p->ntot, p->path, p->logN1, p->logN2);
-  return cuda_status(cudaDeviceSynchronize());
+  if (cudaDeviceSynchronize() != cudaSuccess) return LSP_ERR_CUDA;
+  return p->path == kPathRank1x2 ? s2_upload_desc(p) : LSP_OK;
 }
 
 // setup_path_tables, then (once the norms are known) the K byte index in the new path's order
@@ -535,7 +564,18 @@ int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
   switch (p->path) {
     case kPathMultipass: return multipass_steps_on(p, state, nsteps, s);
     case kPathSmall: return small_steps_on(p, state, nsteps, s);
+    case kPathRank1x2: return s2_steps_on(p, state, nsteps, s);
     default: return s4_steps_on(p, state, nsteps, s);
+  }
+}
+
+// Spectral coefficients of the current state into p->stage (chi order, c128).
+static int path_spectral(lsp_plan p, cudaStream_t s) {
+  switch (p->path) {
+    case kPathMultipass: return multipass_spectral(p, s);
+    case kPathSmall: return small_spectral(p, s);
+    case kPathRank1x2: return s2_spectral(p, s);
+    default: return s4_spectral(p, s);
   }
 }
 
@@ -605,7 +645,8 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   const bool four_first = prec == LSP_C64 && logn0 >= 20;
   const bool small_first = prec == LSP_C64 && r == 1 && logn0 == 13;
   const int order1[] = {small_first ? kPathSmall : four_first ? kPathRank1x4 : kPathMultipass,
-                        four_first ? kPathMultipass : kPathRank1x4, small_first ? kPathMultipass : kPathSmall};
+                        four_first ? kPathMultipass : kPathRank1x4, small_first ? kPathMultipass : kPathSmall,
+                        kPathRank1x2};
   const int order2[] = {kPathSmall, kPathRank2};
   int path = -1;
   if (r == 1) {
@@ -730,7 +771,7 @@ int lsp_strang_steps(lsp_plan p, double dt, int64_t nsteps, void* stream) {
   if (rc) return rc;
   rc = p->path == kPathMultipass ? multipass_steps(p, nsteps, s)
        : p->path == kPathSmall   ? small_steps(p, nsteps, s)
-                                 : s4_steps_on(p, p->u, nsteps, s);
+                                 : path_steps_on(p, p->u, nsteps, s);
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return LSP_OK;
@@ -794,9 +835,7 @@ int lsp_observables(lsp_plan p, double* out, void* stream) {
   if (*p->err_host != 0) return *p->err_host;
   DeviceGuard g(p->device);
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = p->path == kPathMultipass ? multipass_spectral(p, s)
-           : p->path == kPathSmall   ? small_spectral(p, s)
-                                     : s4_spectral(p, s);
+  int rc = path_spectral(p, s);
   if (rc) return rc;
   double* part = nullptr;
   if (cudaMallocAsync((void**)&part, 3 * kObsBlocks * sizeof(double), s) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
@@ -838,9 +877,7 @@ int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device,
   const void* src = p->u;
   int src_prec = p->prec;
   if (space == LSP_SPACE_SPECTRAL) {
-    int rc = p->path == kPathMultipass ? multipass_spectral(p, s)
-             : p->path == kPathSmall   ? small_spectral(p, s)
-                                       : s4_spectral(p, s);
+    int rc = path_spectral(p, s);
     if (rc) return rc;
     src = p->stage;
     src_prec = LSP_C128;
@@ -944,7 +981,7 @@ int lsp_plan_set_wait_limit(lsp_plan p, int64_t polls) {
 
 int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double* ms) {
   if (!p || !ms || nsteps < 2 || nsteps > 4096 || !isfinite(dt)) return LSP_ERR_BAD_ARG;
-  if (p->path != kPathRank2 && p->path != kPathRank1x4) return LSP_ERR_UNSUPPORTED;
+  if (p->path != kPathRank2 && p->path != kPathRank1x4 && p->path != kPathRank1x2) return LSP_ERR_UNSUPPORTED;
   if (*p->err_host != 0) return *p->err_host;
   DeviceGuard g(p->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -954,8 +991,12 @@ int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double*
   int rc = build_phase_tables(p, dt, s);
   if (!rc && cudaMemcpyAsync(scratch, p->u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = LSP_ERR_CUDA;
   double warm[4];
-  if (!rc) rc = s4_sweep_times(p, scratch, nsteps, s, warm);          // warm-up: every kernel once
-  if (!rc) rc = s4_sweep_times(p, scratch, nsteps, s, ms);
+  auto times = [&](double* out) {
+    return p->path == kPathRank1x2 ? s2_sweep_times(p, scratch, nsteps, s, out)
+                                   : s4_sweep_times(p, scratch, nsteps, s, out);
+  };
+  if (!rc) rc = times(warm);                                          // warm-up: every kernel once
+  if (!rc) rc = times(ms);
   if (!rc) {
     int err = 0;
     if (cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = LSP_ERR_CUDA;

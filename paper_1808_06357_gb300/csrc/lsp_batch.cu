@@ -113,7 +113,8 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   for (int i = 0; i < count; ++i) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
     else if (s4_batchable(plans[i])) by_m4[{plans[i]->logn, plans[i]->kidx != nullptr}].push_back(i);
-    else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4) b->seq_ids.push_back(i);
+    else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4 || plans[i]->path == kPathRank1x2)
+      b->seq_ids.push_back(i);
     else by_line[small_line_logn(plans[i])].push_back(i);
   }
   for (auto& kv : by_m4) {
@@ -200,8 +201,10 @@ int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream)
     if (rc) return rc;
   }
   for (int i : b->seq_ids) {     // each fills the GPU by itself
-    int rc = s4_steps_on(b->plans[i], b->plans[i]->u, nsteps, s);
+    lsp_plan p = b->plans[i];
+    int rc = path_steps_on(p, p->u, nsteps, s);
     if (rc) return rc;
+    LSP_CUDA_TRY(cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   }
   for (auto& c : b->classes) {
     int rc = multipass_batch_steps(b->prec, c.m, c.desc, c.colmap, c.rowmap, (int)c.ids.size(), c.total_col,
@@ -216,7 +219,10 @@ int lsp_batch_status(lsp_batch b, void* stream) {
   if (!b) return LSP_ERR_BAD_ARG;
   DeviceGuard g(b->device);
   LSP_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-  return *b->err_host;
+  if (*b->err_host) return *b->err_host;
+  for (int i : b->seq_ids)                 // instances stepped by their own plan's kernels
+    if (*b->plans[i]->err_host) return *b->plans[i]->err_host;
+  return LSP_OK;
 }
 
 void lsp_batch_destroy(lsp_batch b) {

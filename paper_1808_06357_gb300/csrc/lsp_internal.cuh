@@ -34,9 +34,9 @@ constexpr long long kKIdxMax = 256;
 // Bounded device-side waits (grid barrier): spins of ~100 ns each.
 constexpr long long kSpinLimit = 1ll << 25;
 
-// Execution paths (lsp_plan_info [3]): rank-1 two-sweep multipass, SMEM-resident,
-// rank-2 four-sweep, rank-1 four-sweep.
-enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2, kPathRank1x4 = 3, kNumPaths = 4 };
+// Execution paths (lsp_plan_info [3]): rank-1 two-sweep multipass (persistent kernel),
+// SMEM-resident, rank-2 four-sweep, rank-1 four-sweep, rank-1 two-sweep with TMA-fed tiles.
+enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2, kPathRank1x4 = 3, kPathRank1x2 = 4, kNumPaths = 5 };
 
 // --------------------------------------------------------------------------
 // Plan
@@ -119,6 +119,8 @@ struct lsp_plan_s {
   void* stage = nullptr;      // n complex128 staging buffer (conversions, spectral output)
   void* work = nullptr;       // n complex (plan precision): scratch copy for spectral output
   void* desc = nullptr;       // device copies of the multipass kernel descriptors
+  void* s2desc = nullptr;     // TMA two-sweep path: descriptors (state, spectral copy, other buffer)
+  std::vector<unsigned char> s2host0;   // host copy of descriptor slot 0
   int* err_host = nullptr;    // pinned mirror of the device error word
   unsigned* bar = nullptr;    // grid-barrier counter
   int* err = nullptr;         // device error word
@@ -354,6 +356,12 @@ int s4_class_sync(lsp_batch_s::S4Class& c, const std::vector<lsp_plan>& plans, b
 int s4_class_steps(const lsp_batch_s::S4Class& c, int prec, int64_t nsteps, cudaStream_t s);
 void s4_class_free(lsp_batch_s::S4Class& c);
 int s4_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
+// TMA-fed two-sweep rank-1 path (lsp_s2.cu)
+bool s2_supports(int prec, int m);
+int s2_upload_desc(lsp_plan p);                            // after the tables or the K form changed
+int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
+int s2_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
+int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms);
 // steps of the plan's current path on a state buffer of the plan's geometry
 int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 

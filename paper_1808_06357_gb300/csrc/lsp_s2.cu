@@ -1,0 +1,258 @@
+// Host side of the TMA-fed two-sweep rank-1 path: tensor maps, descriptors,
+// launches, the step driver (replayed as a CUDA graph) and spectral output.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include <cudaTypedefs.h>
+
+#include "lsp_s2.cuh"
+
+namespace lsp {
+
+constexpr int kS2MinLog = 20, kS2MaxLog = 23;
+
+static bool s2_lookup(int m, S2Kernels* k) {
+  switch (m) {
+    case 20: *k = s2_kernels<20>(); return true;
+    case 21: *k = s2_kernels<21>(); return true;
+    case 22: *k = s2_kernels<22>(); return true;
+    case 23: *k = s2_kernels<23>(); return true;
+    default: return false;
+  }
+}
+
+bool s2_supports(int prec, int m) { return prec == LSP_C64 && m >= kS2MinLog && m <= kS2MaxLog; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  });
+  return fn;
+}
+
+// 2-D map of an n-point complex64 array viewed as N2 rows of N1 = 4096 elements of 8
+// bytes, copied in boxes of C columns x BR rows.
+static int encode_cols(CUtensorMap* map, const void* base, int m) {
+  auto fn = encode_tiled();
+  if (!fn) return LSP_ERR_CUDA;
+  const int ln2 = m - kS2LogN1;
+  const cuuint64_t dims[2] = {(cuuint64_t)1 << kS2LogN1, (cuuint64_t)1 << ln2};
+  const cuuint64_t strides[1] = {((cuuint64_t)1 << kS2LogN1) * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)(kS2Tile >> ln2), (cuuint32_t)std::min(1 << ln2, 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LSP_OK : LSP_ERR_CUDA;
+}
+
+static int s2_inst(lsp_plan p, void* state, double2* spec, S2Inst* I) {
+  memset(I, 0, sizeof(*I));
+  int rc = encode_cols(&I->tu, state, p->logn);
+  if (!rc) rc = encode_cols(&I->tph, p->Ph, p->logn);
+  if (!rc) rc = encode_cols(&I->tpf, p->Pf, p->logn);
+  if (rc) return rc;
+  I->u = (float2*)state;
+  I->K = (const float2*)p->K;
+  I->kidx = p->kidx;
+  I->klut = (const float2*)p->klut;
+  I->tw_rows = (const float2*)p->tw_pass;
+  I->tw_cols = (const float2*)p->tw_pass + p->twr_entries;
+  I->tw_coarse = (const float2*)p->tw_coarse;
+  I->tw_fine = (const float2*)p->tw_fine;
+  I->spec = spec;
+  I->nlut = p->klut ? (int)p->max_norm2 + 1 : 0;
+  I->inv_n = (float)(1.0 / (double)p->ntot);
+  return LSP_OK;
+}
+
+// Descriptor slots in p->s2desc: 0 the plan's state, 1 the spectral copy (p->work),
+// 2 any other state buffer (rewritten per call, stream-ordered).
+int s2_upload_desc(lsp_plan p) {
+  if (!p->s2desc && cudaMalloc(&p->s2desc, 3 * sizeof(S2Inst)) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
+  S2Inst I[2];
+  int rc = s2_inst(p, p->u, nullptr, &I[0]);
+  if (!rc) rc = s2_inst(p, p->work, (double2*)p->stage, &I[1]);
+  if (rc) return rc;
+  LSP_CUDA_TRY(cudaMemcpy(p->s2desc, I, sizeof(I), cudaMemcpyHostToDevice));
+  p->s2host0.assign((const unsigned char*)&I[0], (const unsigned char*)&I[0] + sizeof(S2Inst));
+  return LSP_OK;
+}
+
+// Grid of one kernel: CTAs resident at once (cached per device and kernel).
+static int s2_grid(const void* fn, size_t smem, int* grid) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> cache;
+  int dev = 0;
+  LSP_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, fn});
+  if (it != cache.end()) { *grid = it->second; return LSP_OK; }
+  int per_sm = 0, sms = 0;
+  LSP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kS2NT, smem));
+  LSP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) return LSP_ERR_UNSUPPORTED;
+  *grid = per_sm * sms;
+  cache[{dev, fn}] = *grid;
+  return LSP_OK;
+}
+
+static int s2_launch(const void* fn, size_t smem, const S2Inst* inst, const int2* map, int ntiles, int* err,
+                     long long spin_limit, cudaStream_t s) {
+  int grid = 0;
+  int rc = s2_grid(fn, smem, &grid);
+  if (rc) return rc;
+  grid = std::max(1, std::min(ntiles, grid));
+  S2Params P{inst, map, ntiles, err, spin_limit};
+  void* args[] = {(void*)&P};
+  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kS2NT), args, smem, s));
+  return LSP_OK;
+}
+
+// Kernel attributes and grids of every kernel of size m, set outside any capture.
+static int s2_prepare(const S2Kernels& K) {
+  int grid = 0, rc = LSP_OK;
+  for (int k = 0; k < kS2Kinds && !rc; ++k) rc = s2_grid(K.k[k], K.smem[k], &grid);
+  if (!rc) rc = s2_grid(K.row_kidx, K.smem_row_kidx, &grid);
+  return rc;
+}
+
+// N steps on the instance(s) of `inst`: head, N row sweeps with N - 1 mid sweeps between them, tail.
+static int s2_launch_steps(const S2Kernels& K, bool kidx, const S2Inst* inst, const int2* map, int ntiles, int* err,
+                           long long spin_limit, int64_t nsteps, cudaStream_t s) {
+  const void* row = kidx ? K.row_kidx : K.k[kS2Row];
+  const size_t row_smem = kidx ? K.smem_row_kidx : K.smem[kS2Row];
+  int rc = s2_launch(K.k[kS2Head], K.smem[kS2Head], inst, map, ntiles, err, spin_limit, s);
+  for (int64_t st = 0; st < nsteps && !rc; ++st) {
+    rc = s2_launch(row, row_smem, inst, map, ntiles, err, spin_limit, s);
+    if (!rc) rc = st + 1 < nsteps ? s2_launch(K.k[kS2Mid], K.smem[kS2Mid], inst, map, ntiles, err, spin_limit, s)
+                                  : s2_launch(K.k[kS2Tail], K.smem[kS2Tail], inst, map, ntiles, err, spin_limit, s);
+  }
+  return rc;
+}
+
+constexpr int64_t kS2GraphMinSteps = 16;
+
+// Steps on `state` (the plan's own state: descriptor slot 0, replayed from a captured graph
+// for calls of 16 steps or more; another buffer: slot 2, plain launches).
+int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
+  S2Kernels K;
+  if (!s2_lookup(p->logn, &K)) return LSP_ERR_UNSUPPORTED;
+  int rc = s2_prepare(K);
+  if (rc) return rc;
+  const S2Inst* d = (const S2Inst*)p->s2desc;
+  const bool kidx = p->kidx != nullptr;
+  S2Inst I;
+  if ((rc = s2_inst(p, state, nullptr, &I))) return rc;
+  if (state != p->u || p->s2host0.size() != sizeof(I) || memcmp(p->s2host0.data(), &I, sizeof(I)) != 0) {
+    // another buffer, or other phase tables (composed steps): descriptor slot 2, stream-ordered
+    LSP_CUDA_TRY(cudaMemcpyAsync((S2Inst*)p->s2desc + 2, &I, sizeof(I), cudaMemcpyHostToDevice, s));
+    return s2_launch_steps(K, kidx, d + 2, nullptr, K.ntiles, p->err, p->spin_limit, nsteps, s);
+  }
+  if (nsteps < kS2GraphMinSteps) return s2_launch_steps(K, kidx, d, nullptr, K.ntiles, p->err, p->spin_limit, nsteps, s);
+  // graph key: nsteps, K form and wait limit (the descriptor itself lives at a fixed address)
+  std::vector<unsigned char> key(sizeof(nsteps) + sizeof(int) + sizeof(long long) + sizeof(void*));
+  const int form = kidx ? 1 : 0;
+  memcpy(key.data(), &nsteps, sizeof(nsteps));
+  memcpy(key.data() + sizeof(nsteps), &form, sizeof(int));
+  memcpy(key.data() + sizeof(nsteps) + sizeof(int), &p->spin_limit, sizeof(long long));
+  memcpy(key.data() + sizeof(nsteps) + sizeof(int) + sizeof(long long), &p->s2desc, sizeof(void*));
+  key.push_back(0x52);                                  // distinct from the four-sweep paths' keys
+  if (!p->s4_graph || key != p->s4_graph_key) {
+    if (p->s4_graph) { cudaGraphExecDestroy(p->s4_graph); p->s4_graph = nullptr; }
+    if (!p->capture) LSP_CUDA_TRY(cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking));
+    LSP_CUDA_TRY(cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal));
+    rc = s2_launch_steps(K, kidx, d, nullptr, K.ntiles, p->err, p->spin_limit, nsteps, p->capture);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->capture, &g);
+    if (rc || ec != cudaSuccess) { if (g) cudaGraphDestroy(g); return rc ? rc : LSP_ERR_CUDA; }
+    const cudaError_t ei = cudaGraphInstantiate(&p->s4_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { p->s4_graph = nullptr; return LSP_ERR_CUDA; }
+    p->s4_graph_key = key;
+  }
+  LSP_CUDA_TRY(cudaGraphLaunch(p->s4_graph, s));
+  return LSP_OK;
+}
+
+// Spectral coefficients of the current state into p->stage (chi order, c128), on p->work.
+int s2_spectral(lsp_plan p, cudaStream_t s) {
+  S2Kernels K;
+  if (!s2_lookup(p->logn, &K)) return LSP_ERR_UNSUPPORTED;
+  int rc = s2_prepare(K);
+  if (rc) return rc;
+  LSP_CUDA_TRY(cudaMemcpyAsync(p->work, p->u, (size_t)p->ntot * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  const S2Inst* d = (const S2Inst*)p->s2desc + 1;
+  rc = s2_launch(K.k[kS2ColFwd], K.smem[kS2ColFwd], d, nullptr, K.ntiles, p->err, p->spin_limit, s);
+  if (!rc) rc = s2_launch(K.k[kS2RowFwd], K.smem[kS2RowFwd], d, nullptr, K.ntiles, p->err, p->spin_limit, s);
+  return rc;
+}
+
+}  // namespace lsp
+
+namespace lsp {
+
+// The launches of s2 steps on `state` with an event after each: ms[0] the mean of the
+// mid column sweeps, ms[2] of the row (K) sweeps; ms[1] = ms[3] = -1 (no such sweeps).
+int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms) {
+  S2Kernels K;
+  if (!s2_lookup(p->logn, &K)) return LSP_ERR_UNSUPPORTED;
+  int rc = s2_prepare(K);
+  if (rc) return rc;
+  S2Inst I;
+  if ((rc = s2_inst(p, state, nullptr, &I))) return rc;
+  S2Inst* d = (S2Inst*)p->s2desc + 2;
+  LSP_CUDA_TRY(cudaMemcpyAsync(d, &I, sizeof(I), cudaMemcpyHostToDevice, s));
+  const bool kidx = p->kidx != nullptr;
+  const void* row = kidx ? K.row_kidx : K.k[kS2Row];
+  const size_t row_smem = kidx ? K.smem_row_kidx : K.smem[kS2Row];
+  std::vector<cudaEvent_t> ev((size_t)(2 * nsteps + 2), nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
+  std::vector<int> kind;                    // 0 mid column sweep, 2 row sweep, -1 head / tail
+  size_t k = 0;
+  auto rec = [&]() { return cudaEventRecord(ev[k++], s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; };
+  if (!rc) rc = rec();
+  if (!rc) rc = s2_launch(K.k[kS2Head], K.smem[kS2Head], d, nullptr, K.ntiles, p->err, p->spin_limit, s);
+  kind.push_back(-1);
+  if (!rc) rc = rec();
+  for (int64_t st = 0; st < nsteps && !rc; ++st) {
+    rc = s2_launch(row, row_smem, d, nullptr, K.ntiles, p->err, p->spin_limit, s);
+    kind.push_back(2);
+    if (!rc) rc = rec();
+    const bool last = st + 1 == nsteps;
+    if (!rc) rc = s2_launch(K.k[last ? kS2Tail : kS2Mid], K.smem[last ? kS2Tail : kS2Mid], d, nullptr, K.ntiles,
+                            p->err, p->spin_limit, s);
+    kind.push_back(last ? -1 : 0);
+    if (!rc) rc = rec();
+  }
+  if (!rc && cudaEventSynchronize(ev[k - 1]) != cudaSuccess) rc = LSP_ERR_CUDA;
+  if (!rc) {
+    double sum[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < kind.size(); ++i) {
+      if (kind[i] < 0) continue;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      sum[kind[i]] += t;
+      cnt[kind[i]] += 1;
+    }
+    for (int c = 0; c < 4; ++c) ms[c] = cnt[c] ? sum[c] / cnt[c] : -1.0;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+}  // namespace lsp

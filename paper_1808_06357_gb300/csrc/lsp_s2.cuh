@@ -1,0 +1,360 @@
+// Two-sweep Strang step for rank-1 lattices of n = 2^M points (complex64), with
+// every tile brought on chip by the TMA engine.
+//
+// The length-n DFT of Thm 1(iii) is split four-step style (eq. Fnx) into rows of
+// N1 = 4096 contiguous points and columns of N2 = n / 4096 points (stride N1):
+// point k = k1 + N1 k2, bin xi = xi2 + N2 xi1,
+//   W_n^{k xi} = W_n^{k1 xi2} W_N1^{k1 xi1} W_N2^{k2 xi2}.
+// One Strang step (eq. StrangTDSE in physical form, Algorithm 1, adjacent
+// potential half-steps merged) is two sweeps over the state:
+//   column sweep (tile: C = 4096 / N2 adjacent columns k1):
+//       conj W_n^{k1 xi2}, IDFT_N2, 1/n, P, DFT_N2, W_n^{k1 xi2}
+//   row sweep (tile: one row xi2):  DFT_N1, K, IDFT_N1
+// with K in the row sweep's native order (position xi1 + N1 xi2 holds bin
+// xi2 + N2 xi1).  A call of N steps runs a head column sweep (P_half, forward
+// half only), N row sweeps and N - 1 mid column sweeps in between, and a tail
+// column sweep (inverse half, P_half): 2 N + 1 launches, replayed as a graph.
+//
+// Each CTA (256 threads, 16 points each, two CTAs per SM) walks its tiles with
+// the next tile's copy in flight: column tiles are 2-D tensor copies (boxes of
+// C columns x up to 256 rows, one tensor map per array), row tiles one 32 KiB
+// bulk copy, the K byte index a 4 KiB bulk copy into the same slot.  A slot
+// that has been read into registers serves as the tile's exchange buffer for
+// the radix-16 passes, so two slots (and one potential-phase buffer for the
+// column sweeps, whose copy is issued at the start of the tile and consumed
+// after the inverse transform) are all the shared memory a CTA holds.  Waits
+// on the copies are bounded: on expiry the sticky error word is set and the
+// CTA leaves at the next tile boundary with no copy in flight.
+#pragma once
+
+#include "lsp_async.cuh"
+#include "lsp_tile.cuh"
+
+namespace lsp {
+
+// Per-instance descriptor in device memory.
+struct S2Inst {                 // 128-byte aligned through its tensor maps
+  CUtensorMap tu;            // state as {N1 (inner), N2} of 8-byte elements, box {C, BR}
+  CUtensorMap tph;           // P_half, same geometry
+  CUtensorMap tpf;           // P_full, same geometry
+  float2* u;
+  const float2* K;           // K in the row sweep's native order (when kidx is null)
+  const uint8_t* kidx;       // ||h||^2 per row position, thread-major within a row (max < 256)
+  const float2* klut;        // K per value of ||h||^2
+  const float2* tw_rows;     // per-pass twiddles of the 4096-point rows
+  const float2* tw_cols;     // per-pass twiddles of the N2-point columns
+  const float2* tw_coarse;   // W_N1^k, k < N1
+  const float2* tw_fine;     // W_n^k, k < N2
+  double2* spec;             // spectral output (chi order)
+  int nlut;
+  float inv_n;
+};
+
+struct S2Params {
+  const S2Inst* inst;        // device array
+  const int2* map;           // launch tile -> (instance, local tile); null for one instance
+  int ntiles;
+  int* err;
+  long long spin_limit;      // polls of a copy wait before it gives up
+};
+
+enum S2Kind { kS2Head = 0, kS2Mid, kS2Tail, kS2ColFwd, kS2Row, kS2RowFwd, kS2Kinds };
+
+constexpr int kS2NT = 256, kS2Tile = 4096, kS2LogN1 = 12;
+constexpr int kS2MinBlocks = 2;
+constexpr unsigned kS2TileBytes = kS2Tile * 8u;
+
+template <int M, int KIND> struct S2Geo {
+  static constexpr bool COL = KIND <= kS2ColFwd;
+  static constexpr int LN2 = M - kS2LogN1;
+  static constexpr int LOGL = COL ? LN2 : kS2LogN1;
+  using G = Line<float2, kS2NT, LOGL, !COL>;
+  static constexpr int LOGC = G::LOGC;                  // lines per tile
+  static constexpr int C = 1 << LOGC;
+  static constexpr int BR = COL ? ((1 << LN2) < 256 ? (1 << LN2) : 256) : 0;   // rows per tensor box
+  static constexpr bool INV_IN = KIND == kS2Mid || KIND == kS2Tail;
+  static constexpr bool FWD = KIND == kS2Head || KIND == kS2Mid || KIND == kS2ColFwd;
+  static constexpr bool HAS_P = KIND == kS2Head || KIND == kS2Mid || KIND == kS2Tail;
+  static_assert(!COL || C >= 2, "a column tile needs at least 16-byte rows (two columns)");
+};
+
+// Shared memory of one CTA: two tile slots (+ the K byte index of a row), the
+// potential-phase tile of the column sweeps, the K table per norm value.
+template <int M, int KIND, bool KIDX> struct S2Smem {
+  using Geo = S2Geo<M, KIND>;
+  static constexpr unsigned KIDX_BYTES = (!Geo::COL && KIDX) ? 4096u : 0u;
+  static constexpr unsigned SLOT = kS2TileBytes + KIDX_BYTES;
+  static constexpr unsigned PBUF = 2 * SLOT;
+  static constexpr unsigned LUT = PBUF + (Geo::HAS_P ? kS2TileBytes : 0u);
+  static constexpr unsigned USED = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);
+  static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
+};
+
+// Bounded wait for phase `parity` of mbarrier b: at most `limit` non-blocking polls
+// ~32 ns apart.  On expiry the error word is set and *fail raised, and the wait goes
+// on (bounded again) so that the copy has landed before the CTA moves on.
+__device__ __forceinline__ void s2_wait(unsigned long long* b, unsigned parity, long long limit, int* err,
+                                       int* fail) {
+  long long spins = 0;
+  while (!mbar_test_wait(b, parity)) {
+    __nanosleep(32);
+    if (++spins > limit) {
+      atomicCAS(err, 0, LSP_ERR_TIMEOUT);
+      *(volatile int*)fail = 1;
+      for (long long k = 0; k < kSpinLimit && !mbar_try_wait(b, parity); ++k) __nanosleep(64);
+      return;
+    }
+  }
+}
+
+// Issue the copies of local tile t of instance I into slot `dst` (thread 0 only).
+template <int M, int KIND, bool KIDX>
+__device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
+  using Geo = S2Geo<M, KIND>;
+  fence_proxy_async();
+  if constexpr (Geo::COL) {
+    mbar_arrive_expect_tx(b, kS2TileBytes);
+    constexpr int NB = (1 << Geo::LN2) / Geo::BR;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      tma_load_2d(dst + (size_t)k * Geo::BR * Geo::C * 8, &I.tu, t * Geo::C, k * Geo::BR, b);
+  } else {
+    mbar_arrive_expect_tx(b, S2Smem<M, KIND, KIDX>::SLOT);
+    bulk_g2s(dst, I.u + ((size_t)t << kS2LogN1), kS2TileBytes, b);
+    if constexpr (KIDX) bulk_g2s(dst + kS2TileBytes, I.kidx + ((size_t)t << kS2LogN1), 4096u, b);
+  }
+}
+
+// The potential-phase tile (same geometry as the state's column tile).
+template <int M, int KIND>
+__device__ __forceinline__ void s2_issue_p(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
+  using Geo = S2Geo<M, KIND>;
+  const CUtensorMap* map = KIND == kS2Mid ? &I.tpf : &I.tph;
+  fence_proxy_async();
+  mbar_arrive_expect_tx(b, kS2TileBytes);
+  constexpr int NB = (1 << Geo::LN2) / Geo::BR;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) tma_load_2d(dst + (size_t)k * Geo::BR * Geo::C * 8, map, t * Geo::C, k * Geo::BR, b);
+}
+
+// W_n^{k1 xi2} from the two-level table: W_N1^{a >> LN2} W_n^{a mod N2}, a = k1 xi2 mod n.
+template <int M>
+__device__ __forceinline__ float2 s2_big_tw(const S2Inst& I, unsigned k1, unsigned xi2) {
+  constexpr int LN2 = M - kS2LogN1;
+  const unsigned a = (k1 * xi2) & ((1u << M) - 1u);
+  return twprod(__ldg(I.tw_coarse + (a >> LN2)), __ldg(I.tw_fine + (a & ((1u << LN2) - 1u))));
+}
+
+// One column tile: lines = columns k1 = c0 + b of N2 points; slot holds the tile row-major
+// (element (b, i) at i C + b), pbuf the potential-phase tile in the same layout.
+template <int M, int KIND>
+__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, const float2* pbuf,
+                                            unsigned long long* mbp, unsigned pparity, const S2Params& P,
+                                            int* fail) {
+  using Geo = S2Geo<M, KIND>;
+  using G = typename Geo::G;
+  constexpr int LOGL = Geo::LOGL, LOGC = Geo::LOGC, LR1 = G::LOGR1, R1 = G::R1;
+  const int c0 = t << LOGC;
+  float2 v[16];
+  int bn, jn;
+  G::template bm<4>(0, bn, jn);
+  if constexpr (Geo::INV_IN) {
+    // natural order (the forward transform's output): rows xi2 = jn + q L/16
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = slot[((jn + (q << (LOGL - 4))) << LOGC) + bn];
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[q * R1 + r] = slot[((j + (r << (LOGL - LR1))) << LOGC) + b];
+    }
+  }
+  __syncthreads();                                      // slot read: it becomes the exchange buffer
+  if constexpr (Geo::INV_IN) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = twmulc(v[q], s2_big_tw<M>(I, c0 + bn, jn + (q << (LOGL - 4))));
+    G::idft(slot, I.tw_cols, v);
+  }
+  if constexpr (Geo::HAS_P) {
+    s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        float2 x = v[q * R1 + r];
+        if constexpr (Geo::INV_IN) x = cscale(x, I.inv_n);
+        v[q * R1 + r] = apply_phase(x, pbuf[((j + (r << (LOGL - LR1))) << LOGC) + b]);
+      }
+    }
+  }
+  if constexpr (Geo::FWD) {
+    G::dft(slot, I.tw_cols, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const unsigned xi2 = jn + (q << (LOGL - 4));
+      stst(I.u + (c0 + bn) + ((size_t)xi2 << kS2LogN1), twmul(v[q], s2_big_tw<M>(I, c0 + bn, xi2)));
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r)
+        stst(I.u + (c0 + b) + ((size_t)(j + (r << (LOGL - LR1))) << kS2LogN1), v[q * R1 + r]);
+    }
+  }
+}
+
+// One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
+// after the state in the slot, thread-major (thread jn's 16 bytes, q = 0..15, together).
+template <int M, int KIND, bool KIDX>
+__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* lut) {
+  using Geo = S2Geo<M, KIND>;
+  using G = typename Geo::G;
+  constexpr int LOGL = kS2LogN1, LR1 = G::LOGR1, R1 = G::R1;
+  float2 v[16];
+  int bn, jn;
+  G::template bm<4>(0, bn, jn);
+#pragma unroll
+  for (int q = 0; q < 16 / R1; ++q) {
+    int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[q * R1 + r] = slot[(b << LOGL) + j + (r << (LOGL - LR1))];
+  }
+  uint4 kb = make_uint4(0, 0, 0, 0);
+  float2 kv[(KIND == kS2Row && !KIDX) ? 16 : 1];
+  if constexpr (KIND == kS2Row) {
+    if constexpr (KIDX) {
+      kb = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(slot) + kS2TileBytes)[jn];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + ((size_t)t << LOGL) + jn + (q << (LOGL - 4)));
+    }
+  }
+  __syncthreads();                                      // slot read: it becomes the exchange buffer
+  G::dft(slot, I.tw_rows, v);
+  if constexpr (KIND == kS2RowFwd) {
+    const int N2 = 1 << (M - kS2LogN1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int xi1 = jn + (q << (LOGL - 4));
+      const float2 x = cscale(v[q], I.inv_n);
+      I.spec[t + (size_t)xi1 * N2] = make_double2((double)x.x, (double)x.y);
+    }
+  } else {
+    if constexpr (KIDX) {
+      const unsigned w[4] = {kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], lut[(w[q >> 2] >> (8 * (q & 3))) & 255u]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
+    }
+    G::idft(slot, I.tw_rows, v);
+#pragma unroll
+    for (int q = 0; q < 16 / R1; ++q) {
+      int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) stst(I.u + ((size_t)t << LOGL) + (b << LOGL) + j + (r << (LOGL - LR1)), v[q * R1 + r]);
+    }
+  }
+}
+
+template <int M, int KIND, bool KIDX = false>
+__global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_constant__ S2Params P) {
+  using Geo = S2Geo<M, KIND>;
+  using SM = S2Smem<M, KIND, KIDX>;
+  extern __shared__ __align__(128) unsigned char smdyn[];
+  unsigned char* smraw = smdyn + ((128u - (smem_u32(smdyn) & 127u)) & 127u);
+  __shared__ __align__(8) unsigned long long mb[3];    // slot 0, slot 1, potential-phase tile
+  __shared__ int fail;
+  const int G = (int)gridDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&mb[0], 1);
+    mbar_init(&mb[1], 1);
+    mbar_init(&mb[2], 1);
+    fail = 0;
+    fence_mbar_init();
+  }
+  float2* lut = reinterpret_cast<float2*>(smraw + SM::LUT);
+  auto inst_of = [&](int tt, int& local) -> const S2Inst& {
+    if (P.map) { const int2 m = P.map[tt]; local = m.y; return P.inst[m.x]; }
+    local = tt;
+    return P.inst[0];
+  };
+  if constexpr (!Geo::COL && KIDX) {
+    // one table per launch: every instance of a batch launch has the same step size here
+    // only when it is a single instance; batches read their own table per tile below
+    if (!P.map)
+      for (int k = threadIdx.x; k < P.inst[0].nlut; k += kS2NT) lut[k] = P.inst[0].klut[k];
+  }
+  __syncthreads();
+  int t = (int)blockIdx.x;
+  if (t >= P.ntiles) return;
+  if (threadIdx.x == 0) {
+    int l;
+    const S2Inst& I0 = inst_of(t, l);
+    s2_issue_tile<M, KIND, KIDX>(I0, l, smraw, &mb[0]);
+  }
+  for (int i = 0; t < P.ntiles; ++i, t += G) {
+    const int s = i & 1;
+    unsigned char* slot = smraw + (size_t)s * SM::SLOT;
+    s2_wait(&mb[s], (unsigned)(i >> 1) & 1u, P.spin_limit, P.err, &fail);
+    int l;
+    const S2Inst& I = inst_of(t, l);
+    if constexpr (!Geo::COL && KIDX) {
+      if (P.map) {                                       // batch: this instance's K table
+        __syncthreads();
+        for (int k = threadIdx.x; k < I.nlut; k += kS2NT) lut[k] = I.klut[k];
+      }
+    }
+    __syncthreads();                                    // tile i - 1 done; the wait above ended in every thread
+    if (*(volatile int*)&fail) break;                   // no copy is in flight here
+    if (threadIdx.x == 0) {
+      if (t + G < P.ntiles) {
+        int ln;
+        const S2Inst& In = inst_of(t + G, ln);
+        s2_issue_tile<M, KIND, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
+      }
+      if constexpr (Geo::HAS_P) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+    }
+    if constexpr (Geo::COL)
+      s2_col_tile<M, KIND>(I, l, reinterpret_cast<float2*>(slot), reinterpret_cast<const float2*>(smraw + SM::PBUF),
+                           &mb[2], (unsigned)i & 1u, P, &fail);
+    else
+      s2_row_tile<M, KIND, KIDX>(I, l, reinterpret_cast<float2*>(slot), lut);
+  }
+}
+
+// Kernel entry points of one lattice size.
+struct S2Kernels {
+  const void* k[kS2Kinds] = {};
+  const void* row_kidx = nullptr;
+  size_t smem[kS2Kinds] = {};
+  size_t smem_row_kidx = 0;
+  int ntiles = 0;                                       // tiles per sweep (both geometries)
+};
+
+template <int M> S2Kernels s2_kernels() {
+  S2Kernels K;
+  K.k[kS2Head] = (const void*)s2_sweep<M, kS2Head>;
+  K.k[kS2Mid] = (const void*)s2_sweep<M, kS2Mid>;
+  K.k[kS2Tail] = (const void*)s2_sweep<M, kS2Tail>;
+  K.k[kS2ColFwd] = (const void*)s2_sweep<M, kS2ColFwd>;
+  K.k[kS2Row] = (const void*)s2_sweep<M, kS2Row>;
+  K.k[kS2RowFwd] = (const void*)s2_sweep<M, kS2RowFwd>;
+  K.row_kidx = (const void*)s2_sweep<M, kS2Row, true>;
+  K.smem[kS2Head] = S2Smem<M, kS2Head, false>::BYTES;
+  K.smem[kS2Mid] = S2Smem<M, kS2Mid, false>::BYTES;
+  K.smem[kS2Tail] = S2Smem<M, kS2Tail, false>::BYTES;
+  K.smem[kS2ColFwd] = S2Smem<M, kS2ColFwd, false>::BYTES;
+  K.smem[kS2Row] = S2Smem<M, kS2Row, false>::BYTES;
+  K.smem[kS2RowFwd] = S2Smem<M, kS2RowFwd, false>::BYTES;
+  K.smem_row_kidx = S2Smem<M, kS2Row, true>::BYTES;
+  K.ntiles = 1 << (M - kS2LogN1);
+  return K;
+}
+
+}  // namespace lsp

@@ -18,13 +18,16 @@ import workloads as w
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_expires_and_plan_recovers(lib):
+@pytest.mark.parametrize("which", ["persistent", "tma"])
+def test_bounded_wait_expires_and_plan_recovers(lib, which):
+    """persistent: the grid barrier and prefetch waits of the two-sweep persistent kernel (2^16);
+    tma: the tile-copy waits of the TMA-fed two-sweep kernels (2^20)."""
     import torch
-    inst = w.c2(16)
+    inst = w.c2(16 if which == "persistent" else 20)
     P = L.lattice_points(inst.Z, inst.n)
     v, u0 = inst.v(P), inst.u0(P)
     plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64")
-    plan.set_path(lib.PATH_MULTIPASS)
+    plan.set_path(lib.PATH_MULTIPASS if which == "persistent" else lib.PATH_RANK1_TMA)
     plan.set_potential(torch.from_numpy(v).cuda())
     plan.set_state(torch.from_numpy(u0).cuda())
     plan.set_wait_limit(1)

@@ -1,0 +1,120 @@
+"""The TMA-fed two-sweep rank-1 path (execution path 4) against the FP64 oracle (GB300).
+
+Rows of 4096 points and columns of n / 4096 points: n = 2^20 .. 2^23 covers column
+tiles of 16, 8, 4 and 2 columns (tensor boxes of 128, 64, 32 and 16 bytes per row).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+from oracle import strang as S
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 5e-5
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _plan(lib, inst, prec="c64"):
+    import torch
+    P = L.lattice_points(inst.Z, inst.n)
+    v, u0 = inst.v(P), inst.u0(P)
+    plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec)
+    plan.set_path(lib.PATH_RANK1_TMA)
+    plan.set_potential(torch.from_numpy(v).cuda())
+    plan.set_state(torch.from_numpy(u0).cuda())
+    return plan, v, u0
+
+
+@pytest.mark.parametrize("m,nsteps", [(20, 20), (21, 7), (22, 17), (23, 3)])
+def test_tma_two_sweep_matches_oracle(lib, m, nsteps):
+    """Every sweep kind of the path (head, row with the byte-index K, mid, tail), plain launches
+    below 16 steps and the replayed graph from 16 on, against the oracle's steps."""
+    inst = w.c2(m)
+    plan, v, u0 = _plan(lib, inst)
+    assert plan.info()["path"] == lib.PATH_RANK1_TMA
+    assert plan.info()["N1"] == 4096 and plan.info()["N2"] == (1 << m) // 4096
+    plan.strang_steps(inst.dt, nsteps)
+    assert plan.status() == 0
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, nsteps)
+    err = _rel(plan.get_state(prec="c128").cpu().numpy(), ref)
+    assert err < TOL64, err
+    # spectral output (column forward sweep, row forward sweep with 1/n) against the oracle
+    spec = plan.get_state(space="spectral", prec="c128").cpu().numpy()
+    assert _rel(spec, S.coeffs(ref, inst.n)) < TOL64
+    plan.destroy()
+
+
+def test_tma_two_sweep_k_table_without_byte_index(lib):
+    """max ||h||^2 >= 256 (d = 4, n = 2^20, the adjoint workload's lattice): K is read from the
+    8-byte table in the row sweep instead of the byte index."""
+    inst = w.c4(20)
+    plan, v, u0 = _plan(lib, inst)
+    assert plan.info()["max_norm2"] >= 256
+    plan.strang_steps(inst.dt, 18)
+    assert plan.status() == 0
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 18)
+    assert _rel(plan.get_state(prec="c128").cpu().numpy(), ref) < TOL64
+    plan.destroy()
+
+
+def test_tma_two_sweep_graph_replay_and_repeated_calls(lib):
+    """Calls of 16 and more steps replay the captured launches; two calls of 20 and one of 3
+    equal 43 oracle steps; a changed step size rebuilds the tables."""
+    inst = w.c2(20)
+    plan, v, u0 = _plan(lib, inst)
+    plan.strang_steps(inst.dt, 20)
+    plan.strang_steps(inst.dt, 20)
+    plan.strang_steps(inst.dt, 3)
+    plan.strang_steps(2 * inst.dt, 16)
+    assert plan.status() == 0
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 43)
+    ref = S.strang(ref, v, norms, inst.n, inst.gamma, 2 * inst.dt, 16)
+    assert _rel(plan.get_state(prec="c128").cpu().numpy(), ref) < TOL64
+    plan.destroy()
+
+
+def test_tma_two_sweep_adjoint_autotune_and_batch(lib):
+    """The path's steps on other state buffers (adjoint checkpoints, autotune scratch) and inside
+    a batch give the same results as the plan's own calls."""
+    import torch
+    inst = w.c2(20)
+    plan, v, u0 = _plan(lib, inst)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    P = L.lattice_points(inst.Z, inst.n)
+    phi = w.gaussian_packet(P, 0.1, [0.6] + [0.5] * (inst.d - 1))
+    J, gv_ref, gu_ref, uN = S.strang_adjoint(u0, v, norms, inst.n, inst.gamma, inst.dt, 12, phi, ckpt=4)
+    lam = torch.from_numpy(2.0 * S.inner(phi, uN) * phi / phi.size).to(torch.complex64).cuda()
+    gv = torch.empty(inst.npoints, dtype=torch.float64, device="cuda")
+    gu = torch.empty(inst.npoints, dtype=torch.complex64, device="cuda")
+    lib.adjoint(plan, inst.dt, 12, lam, gv, gu, 4)
+    assert plan.status() == 0
+    assert _rel(gv.cpu().numpy(), gv_ref) < 2e-4 and _rel(gu.cpu().numpy(), gu_ref) < 2e-4
+    # sweep times: the column and row sweeps of this path, the state untouched
+    before = plan.get_state().clone()
+    t = plan.sweep_times(inst.dt, 8)
+    assert t["P"] > 0 and t["K"] > 0 and t["A"] < 0 and t["A_inv"] < 0
+    assert torch.equal(plan.get_state(), before)
+    # batch: the instance steps through its own path
+    plan.set_state(torch.from_numpy(u0).cuda())
+    b = lib.Batch([plan])
+    b.steps([inst.dt], 25)
+    assert b.status() == 0
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 25)
+    assert _rel(plan.get_state(prec="c128").cpu().numpy(), ref) < TOL64
+    b.destroy()
+    # autotune sees the path and leaves the state alone
+    path, ms = plan.autotune(inst.dt, 20)
+    assert lib.PATH_RANK1_TMA in ms and path in ms
+    assert _rel(plan.get_state(prec="c128").cpu().numpy(), ref) < TOL64
+    plan.destroy()
