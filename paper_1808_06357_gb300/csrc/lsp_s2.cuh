@@ -8,12 +8,17 @@
 // One Strang step (eq. StrangTDSE in physical form, Algorithm 1, adjacent
 // potential half-steps merged) is two sweeps over the state:
 //   column sweep (tile: C = 4096 / N2 adjacent columns k1):
-//       conj W_n^{k1 xi2}, IDFT_N2, 1/n, P, DFT_N2, W_n^{k1 xi2}
-//   row sweep (tile: one row xi2):  DFT_N1, K, IDFT_N1
+//       IDFT_N2, 1/n, P, DFT_N2
+//   row sweep (tile: one row xi2):  W_n^{k1 xi2}, DFT_N1, K, IDFT_N1, conj W_n^{k1 xi2}
 // with K in the row sweep's native order (position xi1 + N1 xi2 holds bin
-// xi2 + N2 xi1).  A call of N steps runs a head column sweep (P_half, forward
-// half only), N row sweeps and N - 1 mid column sweeps in between, and a tail
-// column sweep (inverse half, P_half): 2 N + 1 launches, replayed as a graph.
+// xi2 + N2 xi1).  The four-step twiddle sits in the row sweep, where the row
+// xi2 is fixed: thread j holds k1 = j + 256 r (r = 0..15), so
+//   W_n^{k1 xi2} = W_n^{j xi2} W_n^{256 r xi2},
+// one table value per thread and sixteen per tile (shared memory) instead of a
+// scattered table lookup per point.  A call of N steps runs a head column sweep
+// (P_half, forward half only), N row sweeps and N - 1 mid column sweeps in
+// between, and a tail column sweep (inverse half, P_half): 2 N + 1 launches,
+// replayed as a graph.
 //
 // Each CTA (256 threads, 16 points each, two CTAs per SM) walks its tiles with
 // the next tile's copy in flight: column tiles are 2-D tensor copies (boxes of
@@ -43,8 +48,8 @@ struct S2Inst {                 // 128-byte aligned through its tensor maps
   const float2* klut;        // K per value of ||h||^2
   const float2* tw_rows;     // per-pass twiddles of the 4096-point rows
   const float2* tw_cols;     // per-pass twiddles of the N2-point columns
-  const float2* tw_coarse;   // W_N1^k, k < N1
-  const float2* tw_fine;     // W_n^k, k < N2
+  const float2* tw_coarse;   // W_N1^k, k < N1 (coarse factor of W_n^a)
+  const float2* tw_fine;     // W_n^k, k < N2 (fine factor)
   double2* spec;             // spectral output (chi order)
   int nlut;
   float inv_n;
@@ -86,7 +91,8 @@ template <int M, int KIND, bool KIDX> struct S2Smem {
   static constexpr unsigned SLOT = kS2TileBytes + KIDX_BYTES;
   static constexpr unsigned PBUF = 2 * SLOT;
   static constexpr unsigned LUT = PBUF + (Geo::HAS_P ? kS2TileBytes : 0u);
-  static constexpr unsigned USED = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);
+  static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // W_n^{256 r xi2}, r < 16
+  static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 16u * 8u);
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
 };
 
@@ -137,11 +143,10 @@ __device__ __forceinline__ void s2_issue_p(const S2Inst& I, int t, unsigned char
   for (int k = 0; k < NB; ++k) tma_load_2d(dst + (size_t)k * Geo::BR * Geo::C * 8, map, t * Geo::C, k * Geo::BR, b);
 }
 
-// W_n^{k1 xi2} from the two-level table: W_N1^{a >> LN2} W_n^{a mod N2}, a = k1 xi2 mod n.
+// W_n^a (a < n) from the two-level table: W_N1^{a >> LN2} W_n^{a mod N2}.
 template <int M>
-__device__ __forceinline__ float2 s2_big_tw(const S2Inst& I, unsigned k1, unsigned xi2) {
+__device__ __forceinline__ float2 s2_wn(const S2Inst& I, unsigned a) {
   constexpr int LN2 = M - kS2LogN1;
-  const unsigned a = (k1 * xi2) & ((1u << M) - 1u);
   return twprod(__ldg(I.tw_coarse + (a >> LN2)), __ldg(I.tw_fine + (a & ((1u << LN2) - 1u))));
 }
 
@@ -171,11 +176,7 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
     }
   }
   __syncthreads();                                      // slot read: it becomes the exchange buffer
-  if constexpr (Geo::INV_IN) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = twmulc(v[q], s2_big_tw<M>(I, c0 + bn, jn + (q << (LOGL - 4))));
-    G::idft(slot, I.tw_cols, v);
-  }
+  if constexpr (Geo::INV_IN) G::idft(slot, I.tw_cols, v);
   if constexpr (Geo::HAS_P) {
     s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
 #pragma unroll
@@ -192,10 +193,7 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
   if constexpr (Geo::FWD) {
     G::dft(slot, I.tw_cols, v);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const unsigned xi2 = jn + (q << (LOGL - 4));
-      stst(I.u + (c0 + bn) + ((size_t)xi2 << kS2LogN1), twmul(v[q], s2_big_tw<M>(I, c0 + bn, xi2)));
-    }
+    for (int q = 0; q < 16; ++q) stst(I.u + (c0 + bn) + ((size_t)(jn + (q << (LOGL - 4))) << kS2LogN1), v[q]);
   } else {
 #pragma unroll
     for (int q = 0; q < 16 / R1; ++q) {
@@ -210,19 +208,19 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
 // One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
 // after the state in the slot, thread-major (thread jn's 16 bytes, q = 0..15, together).
 template <int M, int KIND, bool KIDX>
-__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* lut) {
+__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* lut, float2* twr) {
   using Geo = S2Geo<M, KIND>;
   using G = typename Geo::G;
   constexpr int LOGL = kS2LogN1, LR1 = G::LOGR1, R1 = G::R1;
+  static_assert(R1 == 16 && G::C == 1, "rows of 4096 points: one radix-16 butterfly per thread in pass 1");
+  constexpr unsigned NMASK = (1u << M) - 1u;
   float2 v[16];
   int bn, jn;
   G::template bm<4>(0, bn, jn);
+  // pass-1 pattern: register r holds k1 = j + 256 r of row t (j = jn here: one line per tile)
 #pragma unroll
-  for (int q = 0; q < 16 / R1; ++q) {
-    int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-    for (int r = 0; r < R1; ++r) v[q * R1 + r] = slot[(b << LOGL) + j + (r << (LOGL - LR1))];
-  }
+  for (int r = 0; r < 16; ++r) v[r] = slot[jn + (r << (LOGL - 4))];
+  if (threadIdx.x < 16) twr[threadIdx.x] = s2_wn<M>(I, ((unsigned)t * (threadIdx.x << (LOGL - 4))) & NMASK);
   uint4 kb = make_uint4(0, 0, 0, 0);
   float2 kv[(KIND == kS2Row && !KIDX) ? 16 : 1];
   if constexpr (KIND == kS2Row) {
@@ -234,6 +232,10 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
     }
   }
   __syncthreads();                                      // slot read: it becomes the exchange buffer
+  // four-step twiddle W_n^{k1 t} = W_n^{j t} W_n^{256 r t}
+  const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
   G::dft(slot, I.tw_rows, v);
   if constexpr (KIND == kS2RowFwd) {
     const int N2 = 1 << (M - kS2LogN1);
@@ -254,11 +256,7 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
     }
     G::idft(slot, I.tw_rows, v);
 #pragma unroll
-    for (int q = 0; q < 16 / R1; ++q) {
-      int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-      for (int r = 0; r < R1; ++r) stst(I.u + ((size_t)t << LOGL) + (b << LOGL) + j + (r << (LOGL - LR1)), v[q * R1 + r]);
-    }
+    for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)t << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
   }
 }
 
@@ -324,7 +322,8 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
       s2_col_tile<M, KIND>(I, l, reinterpret_cast<float2*>(slot), reinterpret_cast<const float2*>(smraw + SM::PBUF),
                            &mb[2], (unsigned)i & 1u, P, &fail);
     else
-      s2_row_tile<M, KIND, KIDX>(I, l, reinterpret_cast<float2*>(slot), lut);
+      s2_row_tile<M, KIND, KIDX>(I, l, reinterpret_cast<float2*>(slot), lut,
+                                 reinterpret_cast<float2*>(smraw + SM::TWR));
   }
 }
 

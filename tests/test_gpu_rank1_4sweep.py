@@ -88,7 +88,12 @@ def test_paths_set_path_and_errors(lib):
     plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64")
     assert plan.info()["path"] == lib.PATH_RANK1_4SWEEP         # complex64 default from 2^20
     assert lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128").info()["path"] == lib.PATH_MULTIPASS
-    assert set(plan.paths()) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP}
+    assert set(plan.paths()) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP, lib.PATH_RANK1_TMA}
+    c128 = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128")
+    assert set(c128.paths()) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP}    # the TMA path is complex64 only
+    with pytest.raises(lib.LspError) as e:
+        c128.set_path(lib.PATH_RANK1_TMA)
+    assert e.value.code == -8
     with pytest.raises(lib.LspError) as e:
         plan.set_path(lib.PATH_RANK2)
     assert e.value.code == -8
@@ -113,7 +118,7 @@ def test_autotune_keeps_results_and_state(lib):
     plan.set_potential(torch.from_numpy(v).cuda())
     plan.set_state(torch.from_numpy(u0).cuda())
     chosen, ms = plan.autotune(inst.dt, 10)
-    assert set(ms) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP} and all(t > 0 for t in ms.values())
+    assert set(ms) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP} and all(t > 0 for t in ms.values())  # c128
     assert chosen == min(ms, key=ms.get) and plan.info()["path"] == chosen
     assert rel_l2(plan.get_state().cpu().numpy(), u0) == 0.0
     plan.strang_steps(inst.dt, 20)
