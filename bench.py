@@ -536,6 +536,7 @@ def run_ours(args):
                        "path": {0: "two-sweep persistent (4096 x 1024)",
                                 3: "four-sweep (4096 x 32 x 32)",
                                 4: "two-sweep, TMA-fed tiles (4096 x 1024)"}.get(path, str(path)),
+                       "schedule": plan.schedule()[1],
                        "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
                        "autotune_steps": min(100, STEPS_PER_CALL)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

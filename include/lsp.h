@@ -228,15 +228,40 @@ int lsp_plan_set_path(lsp_plan p, int path);
 
 /*
  * lsp_plan_autotune -- time `nsteps` Strang steps of size dt on every
- * available path (after one untimed call of the same length), on a scratch
- * copy of the state (the plan's state is not changed), and keep the fastest.
- * Not in the paper: a schedule choice.
+ * available path and, for path 4, every kernel schedule (after one untimed call
+ * of the same length), on a scratch copy of the state (the plan's state is not
+ * changed), and keep the fastest path and schedule.  The decision is stored
+ * (lsp_autotune_cache) and reused by later plans of the same key without
+ * timing.  Not in the paper: a schedule choice.
  *   chosen  receives the kept path (may be NULL).
- *   ms      NULL, or 5 doubles receiving each path's time in ms (-1: not available).
+ *   ms      NULL, or 5 doubles receiving each path's time in ms, its best schedule's
+ *           for path 4 (-1: not available).
  * Synchronises `stream`.  Errors: BAD_ARG, OOM, CUDA, TIMEOUT (then the plan
  * keeps the path it had).
  */
 int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* chosen, double* ms);
+
+/*
+ * lsp_plan_schedule -- the plan's execution path and kernel schedule.  Path 4 has
+ * three schedules: 0 two CTAs per SM, one exchange buffer, potential-phase tiles
+ * brought in by TMA; 1 two CTAs per SM, two exchange buffers (one barrier per
+ * radix pass), P read directly; 2 three CTAs per SM, one exchange buffer, P read
+ * directly.  Other paths have one schedule (0).  Not in the paper.
+ *   path, sched  receive the values (either may be NULL).  Errors: BAD_ARG.
+ * lsp_plan_set_schedule -- choose a schedule of the current path (results are
+ * the same to rounding).  Errors: BAD_ARG, UNSUPPORTED.
+ */
+int lsp_plan_schedule(lsp_plan p, int* path, int* sched);
+int lsp_plan_set_schedule(lsp_plan p, int sched);
+
+/*
+ * lsp_autotune_cache -- the process-wide store of autotune decisions, keyed by
+ * (device name, precision, rank, moduli, available paths, step count):
+ * lsp_plan_autotune on a plan whose key is stored takes the stored path and
+ * schedule and its times without timing again.  clear != 0 empties the store;
+ * *entries (may be NULL) receives the number of stored decisions.  Always OK.
+ */
+int lsp_autotune_cache(int clear, int64_t* entries);
 
 /*
  * Batched stepping: many independent instances (same precision and device)

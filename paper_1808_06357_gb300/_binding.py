@@ -65,6 +65,9 @@ def _declare(lib):
         "lsp_sweep_times": (I, [P, D, I64, P, P]),
         "lsp_cbc_reconstructing": (I, [P, I64, I, I, P, P, I64, P, C.POINTER(C.c_int), I]),
         "lsp_plan_set_wait_limit": (I, [P, I64]),
+        "lsp_plan_schedule": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "lsp_plan_set_schedule": (I, [P, I]),
+        "lsp_autotune_cache": (I, [I, C.POINTER(C.c_int64)]),
         "lsp_fma_rate": (I, [I, I, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "lsp_strerror": (C.c_char_p, [I]),
     }
@@ -240,6 +243,15 @@ class Plan:
     def status(self, stream=None) -> int:
         return int(self._lib.lsp_plan_status(self._h, _stream_ptr(stream)))
 
+    def schedule(self):
+        """(path, kernel schedule) of the plan (lsp_plan_schedule)."""
+        a, b = C.c_int(), C.c_int()
+        _check(self._lib.lsp_plan_schedule(self._h, C.byref(a), C.byref(b)), "lsp_plan_schedule")
+        return a.value, b.value
+
+    def set_schedule(self, sched: int):
+        _check(self._lib.lsp_plan_set_schedule(self._h, int(sched)), "lsp_plan_set_schedule")
+
     def set_wait_limit(self, polls: int):
         """lsp_plan_set_wait_limit: polls of a bounded device wait before it gives up (0: default)."""
         _check(self._lib.lsp_plan_set_wait_limit(self._h, int(polls)), "lsp_plan_set_wait_limit")
@@ -328,6 +340,14 @@ class Batch:
             self.destroy()
         except Exception:
             pass
+
+
+def autotune_cache(clear: bool = False) -> int:
+    """lsp_autotune_cache: number of stored autotune decisions (emptied first when clear)."""
+    lib = load_library()
+    n = C.c_int64()
+    _check(lib.lsp_autotune_cache(int(bool(clear)), C.byref(n)), "lsp_autotune_cache")
+    return int(n.value)
 
 
 def fma_rate(prec="c128", device: int = 0):

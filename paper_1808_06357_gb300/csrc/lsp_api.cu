@@ -4,8 +4,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "lsp_internal.cuh"
@@ -1006,11 +1011,75 @@ int lsp_sweep_times(lsp_plan p, double dt, int64_t nsteps, void* stream, double*
   return rc;
 }
 
+}  // extern "C"
+
+namespace lsp {
+
+// Autotune decisions, process-wide: key = (device name, precision, rank, moduli, available
+// paths, step count) -> (path, schedule, per-path times).  A plan of the same geometry on
+// the same kind of device takes the stored decision instead of timing again.
+struct TuneEntry {
+  int path = 0, sched = 0;
+  double ms[kNumPaths];
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneEntry> g_tune;
+
+static std::string tune_key(lsp_plan p, int64_t nsteps) {
+  cudaDeviceProp prop;
+  std::string dev = cudaGetDeviceProperties(&prop, p->device) == cudaSuccess ? prop.name : "?";
+  int mask = 0;
+  for (int c = 0; c < kNumPaths; ++c)
+    if (path_available(p, c)) mask |= 1 << c;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "|%d|%d|%lld|%lld|%d|%lld", p->prec, p->r, (long long)p->n[0], (long long)p->n[1], mask,
+           (long long)nsteps);
+  return dev + buf;
+}
+
+// Time one configuration: nsteps on `scratch` (a copy of the state), once untimed (the
+// kernels load and a multi-launch path captures its graph), then timed with events.
+static int time_config(lsp_plan p, double dt, int64_t nsteps, void* scratch, size_t bytes, cudaStream_t s,
+                       cudaEvent_t e0, cudaEvent_t e1, float* t) {
+  int rc = build_phase_tables(p, dt, s);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(scratch, p->u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return LSP_ERR_CUDA;
+  if ((rc = path_steps_on(p, scratch, nsteps, s))) return rc;
+  cudaEventRecord(e0, s);
+  if ((rc = path_steps_on(p, scratch, nsteps, s))) return rc;
+  cudaEventRecord(e1, s);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return LSP_ERR_CUDA;
+  int err = 0;
+  cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err) return err;
+  cudaEventElapsedTime(t, e0, e1);
+  return LSP_OK;
+}
+
+}  // namespace lsp
+
+extern "C" {
+
 int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* chosen, double* ms) {
   if (!p || nsteps < 1 || !isfinite(dt)) return LSP_ERR_BAD_ARG;
   if (*p->err_host != 0) return *p->err_host;
   DeviceGuard g(p->device);
   cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = tune_key(p, nsteps);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      const TuneEntry e = it->second;
+      int rc = LSP_OK;
+      if (e.path != p->path) rc = setup_path(p, e.path);
+      if (!rc) p->s2_sched = e.sched;
+      if (ms)
+        for (int c = 0; c < kNumPaths; ++c) ms[c] = e.ms[c];
+      if (chosen) *chosen = p->path;
+      return rc;
+    }
+  }
   const size_t bytes = (size_t)p->ntot * csize(p->prec);
   if (cudaStreamSynchronize(s) != cudaSuccess) return LSP_ERR_CUDA;
   void* scratch = nullptr;
@@ -1018,29 +1087,23 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int orig = p->path;
-  int best = -1, rc = LSP_OK;
+  const int orig = p->path, orig_sched = p->s2_sched;
+  int best = -1, best_sched = 0, rc = LSP_OK;
   float best_ms = 0.f;
+  TuneEntry entry;
+  for (int c = 0; c < kNumPaths; ++c) entry.ms[c] = -1.0;
   for (int c = 0; c < kNumPaths && !rc; ++c) {
-    if (ms) ms[c] = -1.0;
     if (!path_available(p, c)) continue;
     if (c != p->path && (rc = setup_path(p, c))) break;
-    if ((rc = build_phase_tables(p, dt, s))) break;
-    if (cudaMemcpyAsync(scratch, p->u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
-    // warm-up with the timed call itself: every kernel of the path runs once and a
-    // four-sweep path captures its launch graph outside the timed region
-    if ((rc = path_steps_on(p, scratch, nsteps, s))) break;
-    cudaEventRecord(e0, s);
-    if ((rc = path_steps_on(p, scratch, nsteps, s))) break;
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
-    int err = 0;
-    cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) { rc = err; break; }
-    float t = 0.f;
-    cudaEventElapsedTime(&t, e0, e1);
-    if (ms) ms[c] = t;
-    if (best < 0 || t < best_ms) { best = c; best_ms = t; }
+    // the TMA two-sweep path: every kernel schedule of the size
+    const int nsched = c == kPathRank1x2 ? kS2NumScheds : 1;
+    for (int v = 0; v < nsched && !rc; ++v) {
+      if (c == kPathRank1x2) p->s2_sched = v;
+      float t = 0.f;
+      if ((rc = time_config(p, dt, nsteps, scratch, bytes, s, e0, e1, &t))) break;
+      if (entry.ms[c] < 0 || t < entry.ms[c]) entry.ms[c] = t;
+      if (best < 0 || t < best_ms) { best = c; best_sched = v; best_ms = t; }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1050,8 +1113,39 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
     const int rc2 = setup_path(p, keep);
     if (!rc) rc = rc2;
   }
+  p->s2_sched = rc ? orig_sched : (keep == kPathRank1x2 ? best_sched : 0);
+  if (!rc && best >= 0) {
+    entry.path = best;
+    entry.sched = p->s2_sched;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = entry;
+  }
+  if (ms)
+    for (int c = 0; c < kNumPaths; ++c) ms[c] = entry.ms[c];
   if (chosen) *chosen = p->path;
   return rc;
+}
+
+int lsp_plan_schedule(lsp_plan p, int* path, int* sched) {
+  if (!p) return LSP_ERR_BAD_ARG;
+  if (path) *path = p->path;
+  if (sched) *sched = p->path == kPathRank1x2 ? p->s2_sched : 0;
+  return LSP_OK;
+}
+
+int lsp_plan_set_schedule(lsp_plan p, int sched) {
+  if (!p || sched < 0) return LSP_ERR_BAD_ARG;
+  if (p->path != kPathRank1x2) return sched == 0 ? LSP_OK : LSP_ERR_UNSUPPORTED;
+  if (sched >= kS2NumScheds) return LSP_ERR_UNSUPPORTED;
+  p->s2_sched = sched;
+  return LSP_OK;
+}
+
+int lsp_autotune_cache(int clear, int64_t* entries) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (clear) g_tune.clear();
+  if (entries) *entries = (int64_t)g_tune.size();
+  return LSP_OK;
 }
 
 int lsp_plan_info(lsp_plan p, int64_t* info) {

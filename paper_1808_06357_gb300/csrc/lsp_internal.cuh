@@ -121,6 +121,7 @@ struct lsp_plan_s {
   void* desc = nullptr;       // device copies of the multipass kernel descriptors
   void* s2desc = nullptr;     // TMA two-sweep path: descriptors (state, spectral copy, other buffer)
   std::vector<unsigned char> s2host0;   // host copy of descriptor slot 0
+  int s2_sched = 0;                     // kernel schedule of the TMA two-sweep path (autotuned)
   int* err_host = nullptr;    // pinned mirror of the device error word
   unsigned* bar = nullptr;    // grid-barrier counter
   int* err = nullptr;         // device error word
@@ -357,6 +358,7 @@ int s4_class_steps(const lsp_batch_s::S4Class& c, int prec, int64_t nsteps, cuda
 void s4_class_free(lsp_batch_s::S4Class& c);
 int s4_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
 // TMA-fed two-sweep rank-1 path (lsp_s2.cu)
+constexpr int kS2NumScheds = 3;                            // kernel schedules (lsp_s2.cuh, S2Sched)
 bool s2_supports(int prec, int m);
 int s2_upload_desc(lsp_plan p);                            // after the tables or the K form changed
 int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);

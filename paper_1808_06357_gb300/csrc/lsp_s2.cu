@@ -15,15 +15,22 @@ namespace lsp {
 
 constexpr int kS2MinLog = 20, kS2MaxLog = 23;
 
-static bool s2_lookup(int m, S2Kernels* k) {
+bool s2_kernels_20(int v, S2Kernels* k);
+bool s2_kernels_21(int v, S2Kernels* k);
+bool s2_kernels_22(int v, S2Kernels* k);
+bool s2_kernels_23(int v, S2Kernels* k);
+
+bool s2_kernels_for(int m, int v, S2Kernels* k) {
   switch (m) {
-    case 20: *k = s2_kernels<20>(); return true;
-    case 21: *k = s2_kernels<21>(); return true;
-    case 22: *k = s2_kernels<22>(); return true;
-    case 23: *k = s2_kernels<23>(); return true;
+    case 20: return s2_kernels_20(v, k);
+    case 21: return s2_kernels_21(v, k);
+    case 22: return s2_kernels_22(v, k);
+    case 23: return s2_kernels_23(v, k);
     default: return false;
   }
 }
+
+static bool s2_lookup(lsp_plan p, S2Kernels* k) { return s2_kernels_for(p->logn, p->s2_sched, k); }
 
 bool s2_supports(int prec, int m) { return prec == LSP_C64 && m >= kS2MinLog && m <= kS2MaxLog; }
 
@@ -63,6 +70,8 @@ static int s2_inst(lsp_plan p, void* state, double2* spec, S2Inst* I) {
   if (!rc) rc = encode_cols(&I->tpf, p->Pf, p->logn);
   if (rc) return rc;
   I->u = (float2*)state;
+  I->Ph = (const float2*)p->Ph;
+  I->Pf = (const float2*)p->Pf;
   I->K = (const float2*)p->K;
   I->kidx = p->kidx;
   I->klut = (const float2*)p->klut;
@@ -148,7 +157,7 @@ constexpr int64_t kS2GraphMinSteps = 16;
 // for calls of 16 steps or more; another buffer: slot 2, plain launches).
 int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
   S2Kernels K;
-  if (!s2_lookup(p->logn, &K)) return LSP_ERR_UNSUPPORTED;
+  if (!s2_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
   int rc = s2_prepare(K);
   if (rc) return rc;
   const S2Inst* d = (const S2Inst*)p->s2desc;
@@ -168,6 +177,7 @@ int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
   memcpy(key.data() + sizeof(nsteps), &form, sizeof(int));
   memcpy(key.data() + sizeof(nsteps) + sizeof(int), &p->spin_limit, sizeof(long long));
   memcpy(key.data() + sizeof(nsteps) + sizeof(int) + sizeof(long long), &p->s2desc, sizeof(void*));
+  key.push_back((unsigned char)p->s2_sched);           // the schedule's kernels
   key.push_back(0x52);                                  // distinct from the four-sweep paths' keys
   if (!p->s4_graph || key != p->s4_graph_key) {
     if (p->s4_graph) { cudaGraphExecDestroy(p->s4_graph); p->s4_graph = nullptr; }
@@ -189,7 +199,7 @@ int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
 // Spectral coefficients of the current state into p->stage (chi order, c128), on p->work.
 int s2_spectral(lsp_plan p, cudaStream_t s) {
   S2Kernels K;
-  if (!s2_lookup(p->logn, &K)) return LSP_ERR_UNSUPPORTED;
+  if (!s2_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
   int rc = s2_prepare(K);
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->work, p->u, (size_t)p->ntot * sizeof(float2), cudaMemcpyDeviceToDevice, s));
@@ -207,7 +217,7 @@ namespace lsp {
 // mid column sweeps, ms[2] of the row (K) sweeps; ms[1] = ms[3] = -1 (no such sweeps).
 int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms) {
   S2Kernels K;
-  if (!s2_lookup(p->logn, &K)) return LSP_ERR_UNSUPPORTED;
+  if (!s2_lookup(p, &K)) return LSP_ERR_UNSUPPORTED;
   int rc = s2_prepare(K);
   if (rc) return rc;
   S2Inst I;

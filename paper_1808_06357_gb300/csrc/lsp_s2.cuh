@@ -20,7 +20,7 @@
 // between, and a tail column sweep (inverse half, P_half): 2 N + 1 launches,
 // replayed as a graph.
 //
-// Each CTA (256 threads, 16 points each, two CTAs per SM) walks its tiles with
+// Each CTA (256 threads, 16 points each, two or three CTAs per SM) walks its tiles with
 // the next tile's copy in flight: column tiles are 2-D tensor copies (boxes of
 // C columns x up to 256 rows, one tensor map per array), row tiles one 32 KiB
 // bulk copy, the K byte index a 4 KiB bulk copy into the same slot.  A slot
@@ -43,6 +43,8 @@ struct S2Inst {                 // 128-byte aligned through its tensor maps
   CUtensorMap tph;           // P_half, same geometry
   CUtensorMap tpf;           // P_full, same geometry
   float2* u;
+  const float2* Ph;          // P_half, P_full in point order (schedules that load P directly)
+  const float2* Pf;
   const float2* K;           // K in the row sweep's native order (when kidx is null)
   const uint8_t* kidx;       // ||h||^2 per row position, thread-major within a row (max < 256)
   const float2* klut;        // K per value of ||h||^2
@@ -66,8 +68,20 @@ struct S2Params {
 enum S2Kind { kS2Head = 0, kS2Mid, kS2Tail, kS2ColFwd, kS2Row, kS2RowFwd, kS2Kinds };
 
 constexpr int kS2NT = 256, kS2Tile = 4096, kS2LogN1 = 12;
-constexpr int kS2MinBlocks = 2;
 constexpr unsigned kS2TileBytes = kS2Tile * 8u;
+
+// Schedules of the kernels (the autotuner's choice per lattice size):
+//   0: two CTAs per SM; one exchange buffer (the tile's slot, two barriers per radix
+//      pass); the potential-phase tile of the column sweeps brought in by TMA
+//   1: two CTAs per SM; two exchange buffers (one barrier per radix pass); P read
+//      straight from global memory after the inverse transform
+//   2: three CTAs per SM (at most 80 registers a thread); one exchange buffer; P read
+//      straight from global memory
+template <int V> struct S2Sched;
+template <> struct S2Sched<0> { static constexpr int MINB = 2; static constexpr bool DBX = false, PTMA = true; };
+template <> struct S2Sched<1> { static constexpr int MINB = 2; static constexpr bool DBX = true, PTMA = false; };
+template <> struct S2Sched<2> { static constexpr int MINB = 3; static constexpr bool DBX = false, PTMA = false; };
+static_assert(kS2NumScheds == 3, "schedule count as declared for the host");
 
 template <int M, int KIND> struct S2Geo {
   static constexpr bool COL = KIND <= kS2ColFwd;
@@ -83,14 +97,17 @@ template <int M, int KIND> struct S2Geo {
   static_assert(!COL || C >= 2, "a column tile needs at least 16-byte rows (two columns)");
 };
 
-// Shared memory of one CTA: two tile slots (+ the K byte index of a row), the
-// potential-phase tile of the column sweeps, the K table per norm value.
-template <int M, int KIND, bool KIDX> struct S2Smem {
+// Shared memory of one CTA: two tile slots (+ the K byte index of a row), the second
+// exchange buffer, the potential-phase tile, the K table per norm value, the sixteen
+// per-tile twiddles of a row.
+template <int M, int KIND, bool KIDX, int V> struct S2Smem {
   using Geo = S2Geo<M, KIND>;
+  using SC = S2Sched<V>;
   static constexpr unsigned KIDX_BYTES = (!Geo::COL && KIDX) ? 4096u : 0u;
   static constexpr unsigned SLOT = kS2TileBytes + KIDX_BYTES;
-  static constexpr unsigned PBUF = 2 * SLOT;
-  static constexpr unsigned LUT = PBUF + (Geo::HAS_P ? kS2TileBytes : 0u);
+  static constexpr unsigned XB = 2 * SLOT;
+  static constexpr unsigned PBUF = XB + (SC::DBX ? kS2TileBytes : 0u);
+  static constexpr unsigned LUT = PBUF + ((Geo::HAS_P && SC::PTMA) ? kS2TileBytes : 0u);
   static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // W_n^{256 r xi2}, r < 16
   static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 16u * 8u);
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
@@ -125,7 +142,7 @@ __device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned c
     for (int k = 0; k < NB; ++k)
       tma_load_2d(dst + (size_t)k * Geo::BR * Geo::C * 8, &I.tu, t * Geo::C, k * Geo::BR, b);
   } else {
-    mbar_arrive_expect_tx(b, S2Smem<M, KIND, KIDX>::SLOT);
+    mbar_arrive_expect_tx(b, kS2TileBytes + (KIDX ? 4096u : 0u));
     bulk_g2s(dst, I.u + ((size_t)t << kS2LogN1), kS2TileBytes, b);
     if constexpr (KIDX) bulk_g2s(dst + kS2TileBytes, I.kidx + ((size_t)t << kS2LogN1), 4096u, b);
   }
@@ -150,10 +167,23 @@ __device__ __forceinline__ float2 s2_wn(const S2Inst& I, unsigned a) {
   return twprod(__ldg(I.tw_coarse + (a >> LN2)), __ldg(I.tw_fine + (a & ((1u << LN2) - 1u))));
 }
 
+// Forward / inverse line transform of a tile with one or two exchange buffers (schedule V);
+// PAR continues the alternation of two buffers within a tile.
+template <typename G, int V, int PAR>
+__device__ __forceinline__ void s2_dft(float2* a, float2* b, const float2* tw, float2 (&v)[16]) {
+  if constexpr (S2Sched<V>::DBX) G::template dft2<PAR>(a, b, tw, v);
+  else G::dft(a, tw, v);
+}
+template <typename G, int V, int PAR>
+__device__ __forceinline__ void s2_idft(float2* a, float2* b, const float2* tw, float2 (&v)[16]) {
+  if constexpr (S2Sched<V>::DBX) G::template idft2<PAR>(a, b, tw, v);
+  else G::idft(a, tw, v);
+}
+
 // One column tile: lines = columns k1 = c0 + b of N2 points; slot holds the tile row-major
-// (element (b, i) at i C + b), pbuf the potential-phase tile in the same layout.
-template <int M, int KIND>
-__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, const float2* pbuf,
+// (element (b, i) at i C + b), pbuf the potential-phase tile in the same layout (schedule 0).
+template <int M, int KIND, int V>
+__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, float2* xb, const float2* pbuf,
                                             unsigned long long* mbp, unsigned pparity, const S2Params& P,
                                             int* fail) {
   using Geo = S2Geo<M, KIND>;
@@ -175,10 +205,11 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
       for (int r = 0; r < R1; ++r) v[q * R1 + r] = slot[((j + (r << (LOGL - LR1))) << LOGC) + b];
     }
   }
-  __syncthreads();                                      // slot read: it becomes the exchange buffer
-  if constexpr (Geo::INV_IN) G::idft(slot, I.tw_cols, v);
+  __syncthreads();                                      // slot read: it becomes an exchange buffer
+  if constexpr (Geo::INV_IN) s2_idft<G, V, 0>(slot, xb, I.tw_cols, v);
   if constexpr (Geo::HAS_P) {
-    s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
+    const float2* ptab = KIND == kS2Mid ? I.Pf : I.Ph;
+    if constexpr (S2Sched<V>::PTMA) s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
 #pragma unroll
     for (int q = 0; q < 16 / R1; ++q) {
       int b, j; G::template bm<LR1>(q, b, j);
@@ -186,12 +217,14 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
       for (int r = 0; r < R1; ++r) {
         float2 x = v[q * R1 + r];
         if constexpr (Geo::INV_IN) x = cscale(x, I.inv_n);
-        v[q * R1 + r] = apply_phase(x, pbuf[((j + (r << (LOGL - LR1))) << LOGC) + b]);
+        const int i = j + (r << (LOGL - LR1));
+        const float2 e = S2Sched<V>::PTMA ? pbuf[(i << LOGC) + b] : ldtab(ptab + (c0 + b) + ((size_t)i << kS2LogN1));
+        v[q * R1 + r] = apply_phase(x, e);
       }
     }
   }
   if constexpr (Geo::FWD) {
-    G::dft(slot, I.tw_cols, v);
+    s2_dft<G, V, Geo::INV_IN ? (G::NX & 1) : 0>(slot, xb, I.tw_cols, v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) stst(I.u + (c0 + bn) + ((size_t)(jn + (q << (LOGL - 4))) << kS2LogN1), v[q]);
   } else {
@@ -207,12 +240,13 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
 
 // One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
 // after the state in the slot, thread-major (thread jn's 16 bytes, q = 0..15, together).
-template <int M, int KIND, bool KIDX>
-__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* lut, float2* twr) {
+template <int M, int KIND, bool KIDX, int V>
+__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, float2* xb, const float2* lut,
+                                            float2* twr) {
   using Geo = S2Geo<M, KIND>;
   using G = typename Geo::G;
-  constexpr int LOGL = kS2LogN1, LR1 = G::LOGR1, R1 = G::R1;
-  static_assert(R1 == 16 && G::C == 1, "rows of 4096 points: one radix-16 butterfly per thread in pass 1");
+  constexpr int LOGL = kS2LogN1;
+  static_assert(G::R1 == 16 && G::C == 1, "rows of 4096 points: one radix-16 butterfly per thread in pass 1");
   constexpr unsigned NMASK = (1u << M) - 1u;
   float2 v[16];
   int bn, jn;
@@ -231,12 +265,12 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
       for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + ((size_t)t << LOGL) + jn + (q << (LOGL - 4)));
     }
   }
-  __syncthreads();                                      // slot read: it becomes the exchange buffer
+  __syncthreads();                                      // slot read: it becomes an exchange buffer
   // four-step twiddle W_n^{k1 t} = W_n^{j t} W_n^{256 r t}
   const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
-  G::dft(slot, I.tw_rows, v);
+  s2_dft<G, V, 0>(slot, xb, I.tw_rows, v);
   if constexpr (KIND == kS2RowFwd) {
     const int N2 = 1 << (M - kS2LogN1);
 #pragma unroll
@@ -254,16 +288,17 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
     }
-    G::idft(slot, I.tw_rows, v);
+    s2_idft<G, V, G::NX & 1>(slot, xb, I.tw_rows, v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)t << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
   }
 }
 
-template <int M, int KIND, bool KIDX = false>
-__global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_constant__ S2Params P) {
+template <int M, int KIND, bool KIDX, int V>
+__global__ void __launch_bounds__(kS2NT, S2Sched<V>::MINB) s2_sweep(const __grid_constant__ S2Params P) {
   using Geo = S2Geo<M, KIND>;
-  using SM = S2Smem<M, KIND, KIDX>;
+  using SM = S2Smem<M, KIND, KIDX, V>;
+  constexpr bool PT = Geo::HAS_P && S2Sched<V>::PTMA;   // potential-phase tile by TMA
   extern __shared__ __align__(128) unsigned char smdyn[];
   unsigned char* smraw = smdyn + ((128u - (smem_u32(smdyn) & 127u)) & 127u);
   __shared__ __align__(8) unsigned long long mb[3];    // slot 0, slot 1, potential-phase tile
@@ -277,14 +312,14 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
     fence_mbar_init();
   }
   float2* lut = reinterpret_cast<float2*>(smraw + SM::LUT);
+  float2* xb = reinterpret_cast<float2*>(smraw + SM::XB);
   auto inst_of = [&](int tt, int& local) -> const S2Inst& {
     if (P.map) { const int2 m = P.map[tt]; local = m.y; return P.inst[m.x]; }
     local = tt;
     return P.inst[0];
   };
   if constexpr (!Geo::COL && KIDX) {
-    // one table per launch: every instance of a batch launch has the same step size here
-    // only when it is a single instance; batches read their own table per tile below
+    // one instance: its K table once; a batch reloads the table of each tile's instance below
     if (!P.map)
       for (int k = threadIdx.x; k < P.inst[0].nlut; k += kS2NT) lut[k] = P.inst[0].klut[k];
   }
@@ -316,18 +351,18 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
         const S2Inst& In = inst_of(t + G, ln);
         s2_issue_tile<M, KIND, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
       }
-      if constexpr (Geo::HAS_P) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+      if constexpr (PT) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
     }
     if constexpr (Geo::COL)
-      s2_col_tile<M, KIND>(I, l, reinterpret_cast<float2*>(slot), reinterpret_cast<const float2*>(smraw + SM::PBUF),
-                           &mb[2], (unsigned)i & 1u, P, &fail);
+      s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), xb,
+                              reinterpret_cast<const float2*>(smraw + SM::PBUF), &mb[2], (unsigned)i & 1u, P, &fail);
     else
-      s2_row_tile<M, KIND, KIDX>(I, l, reinterpret_cast<float2*>(slot), lut,
-                                 reinterpret_cast<float2*>(smraw + SM::TWR));
+      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), xb, lut,
+                                    reinterpret_cast<float2*>(smraw + SM::TWR));
   }
 }
 
-// Kernel entry points of one lattice size.
+// Kernel entry points of one lattice size and schedule.
 struct S2Kernels {
   const void* k[kS2Kinds] = {};
   const void* row_kidx = nullptr;
@@ -336,24 +371,36 @@ struct S2Kernels {
   int ntiles = 0;                                       // tiles per sweep (both geometries)
 };
 
-template <int M> S2Kernels s2_kernels() {
+template <int M, int V> S2Kernels s2_kernels_v() {
   S2Kernels K;
-  K.k[kS2Head] = (const void*)s2_sweep<M, kS2Head>;
-  K.k[kS2Mid] = (const void*)s2_sweep<M, kS2Mid>;
-  K.k[kS2Tail] = (const void*)s2_sweep<M, kS2Tail>;
-  K.k[kS2ColFwd] = (const void*)s2_sweep<M, kS2ColFwd>;
-  K.k[kS2Row] = (const void*)s2_sweep<M, kS2Row>;
-  K.k[kS2RowFwd] = (const void*)s2_sweep<M, kS2RowFwd>;
-  K.row_kidx = (const void*)s2_sweep<M, kS2Row, true>;
-  K.smem[kS2Head] = S2Smem<M, kS2Head, false>::BYTES;
-  K.smem[kS2Mid] = S2Smem<M, kS2Mid, false>::BYTES;
-  K.smem[kS2Tail] = S2Smem<M, kS2Tail, false>::BYTES;
-  K.smem[kS2ColFwd] = S2Smem<M, kS2ColFwd, false>::BYTES;
-  K.smem[kS2Row] = S2Smem<M, kS2Row, false>::BYTES;
-  K.smem[kS2RowFwd] = S2Smem<M, kS2RowFwd, false>::BYTES;
-  K.smem_row_kidx = S2Smem<M, kS2Row, true>::BYTES;
+  K.k[kS2Head] = (const void*)s2_sweep<M, kS2Head, false, V>;
+  K.k[kS2Mid] = (const void*)s2_sweep<M, kS2Mid, false, V>;
+  K.k[kS2Tail] = (const void*)s2_sweep<M, kS2Tail, false, V>;
+  K.k[kS2ColFwd] = (const void*)s2_sweep<M, kS2ColFwd, false, V>;
+  K.k[kS2Row] = (const void*)s2_sweep<M, kS2Row, false, V>;
+  K.k[kS2RowFwd] = (const void*)s2_sweep<M, kS2RowFwd, false, V>;
+  K.row_kidx = (const void*)s2_sweep<M, kS2Row, true, V>;
+  K.smem[kS2Head] = S2Smem<M, kS2Head, false, V>::BYTES;
+  K.smem[kS2Mid] = S2Smem<M, kS2Mid, false, V>::BYTES;
+  K.smem[kS2Tail] = S2Smem<M, kS2Tail, false, V>::BYTES;
+  K.smem[kS2ColFwd] = S2Smem<M, kS2ColFwd, false, V>::BYTES;
+  K.smem[kS2Row] = S2Smem<M, kS2Row, false, V>::BYTES;
+  K.smem[kS2RowFwd] = S2Smem<M, kS2RowFwd, false, V>::BYTES;
+  K.smem_row_kidx = S2Smem<M, kS2Row, true, V>::BYTES;
   K.ntiles = 1 << (M - kS2LogN1);
   return K;
 }
+
+template <int M> bool s2_kernels_m(int v, S2Kernels* k) {
+  switch (v) {
+    case 0: *k = s2_kernels_v<M, 0>(); return true;
+    case 1: *k = s2_kernels_v<M, 1>(); return true;
+    case 2: *k = s2_kernels_v<M, 2>(); return true;
+    default: return false;
+  }
+}
+
+// Defined by the instantiation units (one per lattice size); false for other sizes.
+bool s2_kernels_for(int m, int v, S2Kernels* k);
 
 }  // namespace lsp

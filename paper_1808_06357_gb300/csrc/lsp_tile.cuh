@@ -297,6 +297,43 @@ struct Line {
       for (int i = 0; i < 16; ++i) v[i] = w[i];
     }
   }
+  // The same transforms with the exchanges alternating between two buffers a, b:
+  // exchange k of a call goes through buffer (PAR + k) & 1, so a buffer is written
+  // again only two exchanges after it was read, with a barrier in between, and each
+  // exchange needs one barrier instead of two.  The caller guarantees that no thread
+  // still reads the buffer of the call's first exchange; a call that follows another
+  // within a tile continues the alternation (PAR = parity after the previous call).
+  static constexpr int NX = P - 1;                     // exchanges of one transform
+  template <int PAR, int S = 1>
+  static __device__ __forceinline__ void dft2(T* a, T* b, const T* tw, T (&v)[16]) {
+    if constexpr (S > 1) read_in<S>(((PAR + S - 2) & 1) ? b : a, v);
+    fwd_body<S>(tw, v);
+    if constexpr (S < P) {
+      write_out<S>(((PAR + S - 1) & 1) ? b : a, v);
+      sync();
+      dft2<PAR, S + 1>(a, b, tw, v);
+    } else {
+      constexpr int R = 1 << radix_log(S);
+      T w[16];
+#pragma unroll
+      for (int q = 0; q < 16 / R; ++q)
+#pragma unroll
+        for (int t = 0; t < R; ++t) w[q * R + t] = v[q * R + out_at<R>(t)];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = w[i];
+    }
+  }
+  template <int PAR, int S = P>
+  static __device__ __forceinline__ void idft2(T* a, T* b, const T* tw, T (&v)[16]) {
+    if constexpr (S < P) read_out<S>(((PAR + P - S - 1) & 1) ? b : a, v);
+    inv_body<S>(tw, v);
+    if constexpr (S > 1) {
+      write_in<S>(((PAR + P - S) & 1) ? b : a, v);
+      sync();
+      idft2<PAR, S - 1>(a, b, tw, v);
+    }
+  }
+
   // Inverse line DFT (unnormalised): registers holding the last forward
   // pass' outputs in natural order -> the pass-1 input pattern.
   template <int S = P>

@@ -53,6 +53,49 @@ def test_tma_two_sweep_matches_oracle(lib, m, nsteps):
     plan.destroy()
 
 
+@pytest.mark.parametrize("sched", [0, 1, 2])
+@pytest.mark.parametrize("m", [20, 22])
+def test_every_schedule_matches_oracle(lib, m, sched):
+    """The three kernel schedules (exchange buffers, CTAs per SM, P by TMA or direct loads) give
+    the oracle's result: 19 steps (graph replay), spectral output included."""
+    inst = w.c2(m)
+    plan, v, u0 = _plan(lib, inst)
+    plan.set_schedule(sched)
+    assert plan.schedule() == (lib.PATH_RANK1_TMA, sched)
+    plan.strang_steps(inst.dt, 19)
+    assert plan.status() == 0
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 19)
+    assert _rel(plan.get_state(prec="c128").cpu().numpy(), ref) < TOL64
+    assert _rel(plan.get_state(space="spectral", prec="c128").cpu().numpy(), S.coeffs(ref, inst.n)) < TOL64
+    with pytest.raises(lib.LspError):
+        plan.set_schedule(3)
+    plan.destroy()
+
+
+def test_autotune_decision_is_cached_across_plans(lib):
+    """The first plan of a geometry is timed on every path and schedule; a second plan of the same
+    geometry takes the stored decision (same path, schedule and times) without timing."""
+    import torch
+    lib.autotune_cache(clear=True)
+    inst = w.c2(20)
+    a, v, u0 = _plan(lib, inst)
+    pa, ms_a = a.autotune(inst.dt, 20)
+    assert lib.autotune_cache() == 1
+    assert lib.PATH_RANK1_TMA in ms_a and all(t > 0 for t in ms_a.values())
+    b = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64")
+    b.set_potential(torch.from_numpy(v).cuda())
+    b.set_state(torch.from_numpy(u0).cuda())
+    pb, ms_b = b.autotune(inst.dt, 20)
+    assert lib.autotune_cache() == 1
+    assert (pb, ms_b) == (pa, ms_a) and b.schedule() == a.schedule()
+    b.strang_steps(inst.dt, 5)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    assert _rel(b.get_state(prec="c128").cpu().numpy(), S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 5)) < TOL64
+    a.destroy()
+    b.destroy()
+
+
 def test_tma_two_sweep_k_table_without_byte_index(lib):
     """max ||h||^2 >= 256 (d = 4, n = 2^20, the adjoint workload's lattice): K is read from the
     8-byte table in the row sweep instead of the byte index."""
