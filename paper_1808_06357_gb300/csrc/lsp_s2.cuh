@@ -71,23 +71,22 @@ constexpr int kS2NT = 256, kS2Tile = 4096, kS2LogN1 = 12;
 constexpr unsigned kS2TileBytes = kS2Tile * 8u;
 
 // Schedules of the kernels (the autotuner's choice per lattice size):
-//   0: two CTAs per SM; one exchange buffer (the tile's slot, two barriers per radix
-//      pass); the potential-phase tile of the column sweeps brought in by TMA
-//   1: two CTAs per SM; two exchange buffers (one barrier per radix pass); P read
-//      straight from global memory after the inverse transform
-//   2: three CTAs per SM (at most 80 registers a thread); one exchange buffer; P read
-//      straight from global memory
+//   0: two CTAs per SM; the line twiddle tables read through L1; the potential-phase
+//      tile of the column sweeps brought in by TMA
+//   1: as 0, with the line twiddle tables copied into shared memory at the start
+//   2: three CTAs per SM (at most 80 registers a thread); P read straight from
+//      global memory after the inverse transform
 template <int V> struct S2Sched;
-template <> struct S2Sched<0> { static constexpr int MINB = 2; static constexpr bool DBX = false, PTMA = true; };
-template <> struct S2Sched<1> { static constexpr int MINB = 2; static constexpr bool DBX = true, PTMA = false; };
-template <> struct S2Sched<2> { static constexpr int MINB = 3; static constexpr bool DBX = false, PTMA = false; };
+template <> struct S2Sched<0> { static constexpr int MINB = 2; static constexpr bool TWS = false, PTMA = true; };
+template <> struct S2Sched<1> { static constexpr int MINB = 2; static constexpr bool TWS = true, PTMA = true; };
+template <> struct S2Sched<2> { static constexpr int MINB = 3; static constexpr bool TWS = false, PTMA = false; };
 static_assert(kS2NumScheds == 3, "schedule count as declared for the host");
 
 template <int M, int KIND> struct S2Geo {
   static constexpr bool COL = KIND <= kS2ColFwd;
   static constexpr int LN2 = M - kS2LogN1;
   static constexpr int LOGL = COL ? LN2 : kS2LogN1;
-  using G = Line<float2, kS2NT, LOGL, !COL>;
+  using G = Line<float2, kS2NT, LOGL, !COL, 1, COL ? col_swizzle(LOGL) : 0>;
   static constexpr int LOGC = G::LOGC;                  // lines per tile
   static constexpr int C = 1 << LOGC;
   static constexpr int BR = COL ? ((1 << LN2) < 256 ? (1 << LN2) : 256) : 0;   // rows per tensor box
@@ -97,17 +96,17 @@ template <int M, int KIND> struct S2Geo {
   static_assert(!COL || C >= 2, "a column tile needs at least 16-byte rows (two columns)");
 };
 
-// Shared memory of one CTA: two tile slots (+ the K byte index of a row), the second
-// exchange buffer, the potential-phase tile, the K table per norm value, the sixteen
-// per-tile twiddles of a row.
+// Shared memory of one CTA: two tile slots (+ the K byte index of a row), the
+// potential-phase tile, the line twiddles (schedule 1), the K table per norm value,
+// the sixteen per-tile twiddles of a row.
 template <int M, int KIND, bool KIDX, int V> struct S2Smem {
   using Geo = S2Geo<M, KIND>;
   using SC = S2Sched<V>;
   static constexpr unsigned KIDX_BYTES = (!Geo::COL && KIDX) ? 4096u : 0u;
   static constexpr unsigned SLOT = kS2TileBytes + KIDX_BYTES;
-  static constexpr unsigned XB = 2 * SLOT;
-  static constexpr unsigned PBUF = XB + (SC::DBX ? kS2TileBytes : 0u);
-  static constexpr unsigned LUT = PBUF + ((Geo::HAS_P && SC::PTMA) ? kS2TileBytes : 0u);
+  static constexpr unsigned PBUF = 2 * SLOT;
+  static constexpr unsigned TWS = PBUF + ((Geo::HAS_P && SC::PTMA) ? kS2TileBytes : 0u);
+  static constexpr unsigned LUT = TWS + (SC::TWS ? (unsigned)Geo::G::TW_ENTRIES * 8u : 0u);
   static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // W_n^{256 r xi2}, r < 16
   static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 16u * 8u);
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
@@ -167,23 +166,10 @@ __device__ __forceinline__ float2 s2_wn(const S2Inst& I, unsigned a) {
   return twprod(__ldg(I.tw_coarse + (a >> LN2)), __ldg(I.tw_fine + (a & ((1u << LN2) - 1u))));
 }
 
-// Forward / inverse line transform of a tile with one or two exchange buffers (schedule V);
-// PAR continues the alternation of two buffers within a tile.
-template <typename G, int V, int PAR>
-__device__ __forceinline__ void s2_dft(float2* a, float2* b, const float2* tw, float2 (&v)[16]) {
-  if constexpr (S2Sched<V>::DBX) G::template dft2<PAR>(a, b, tw, v);
-  else G::dft(a, tw, v);
-}
-template <typename G, int V, int PAR>
-__device__ __forceinline__ void s2_idft(float2* a, float2* b, const float2* tw, float2 (&v)[16]) {
-  if constexpr (S2Sched<V>::DBX) G::template idft2<PAR>(a, b, tw, v);
-  else G::idft(a, tw, v);
-}
-
 // One column tile: lines = columns k1 = c0 + b of N2 points; slot holds the tile row-major
 // (element (b, i) at i C + b), pbuf the potential-phase tile in the same layout (schedule 0).
 template <int M, int KIND, int V>
-__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, float2* xb, const float2* pbuf,
+__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* pbuf,
                                             unsigned long long* mbp, unsigned pparity, const S2Params& P,
                                             int* fail) {
   using Geo = S2Geo<M, KIND>;
@@ -206,7 +192,7 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
     }
   }
   __syncthreads();                                      // slot read: it becomes an exchange buffer
-  if constexpr (Geo::INV_IN) s2_idft<G, V, 0>(slot, xb, I.tw_cols, v);
+  if constexpr (Geo::INV_IN) G::idft(slot, tw, v);
   if constexpr (Geo::HAS_P) {
     const float2* ptab = KIND == kS2Mid ? I.Pf : I.Ph;
     if constexpr (S2Sched<V>::PTMA) s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
@@ -224,7 +210,7 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
     }
   }
   if constexpr (Geo::FWD) {
-    s2_dft<G, V, Geo::INV_IN ? (G::NX & 1) : 0>(slot, xb, I.tw_cols, v);
+    G::dft(slot, tw, v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) stst(I.u + (c0 + bn) + ((size_t)(jn + (q << (LOGL - 4))) << kS2LogN1), v[q]);
   } else {
@@ -241,7 +227,7 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
 // One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
 // after the state in the slot, thread-major (thread jn's 16 bytes, q = 0..15, together).
 template <int M, int KIND, bool KIDX, int V>
-__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, float2* xb, const float2* lut,
+__device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* lut,
                                             float2* twr) {
   using Geo = S2Geo<M, KIND>;
   using G = typename Geo::G;
@@ -270,7 +256,7 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
   const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
-  s2_dft<G, V, 0>(slot, xb, I.tw_rows, v);
+  G::dft(slot, tw, v);
   if constexpr (KIND == kS2RowFwd) {
     const int N2 = 1 << (M - kS2LogN1);
 #pragma unroll
@@ -288,7 +274,7 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
     }
-    s2_idft<G, V, G::NX & 1>(slot, xb, I.tw_rows, v);
+    G::idft(slot, tw, v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)t << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
   }
@@ -312,7 +298,14 @@ __global__ void __launch_bounds__(kS2NT, S2Sched<V>::MINB) s2_sweep(const __grid
     fence_mbar_init();
   }
   float2* lut = reinterpret_cast<float2*>(smraw + SM::LUT);
-  float2* xb = reinterpret_cast<float2*>(smraw + SM::XB);
+  // line twiddles: shared-memory copy (schedule 1) or the table in global memory; every
+  // instance of a launch has the same line length, hence the same table
+  const float2* tw = Geo::COL ? P.inst[0].tw_cols : P.inst[0].tw_rows;
+  if constexpr (S2Sched<V>::TWS) {
+    float2* tws = reinterpret_cast<float2*>(smraw + SM::TWS);
+    for (int k = threadIdx.x; k < Geo::G::TW_ENTRIES; k += kS2NT) tws[k] = __ldg(tw + k);
+    tw = tws;
+  }
   auto inst_of = [&](int tt, int& local) -> const S2Inst& {
     if (P.map) { const int2 m = P.map[tt]; local = m.y; return P.inst[m.x]; }
     local = tt;
@@ -354,10 +347,10 @@ __global__ void __launch_bounds__(kS2NT, S2Sched<V>::MINB) s2_sweep(const __grid
       if constexpr (PT) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
     }
     if constexpr (Geo::COL)
-      s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), xb,
+      s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), tw,
                               reinterpret_cast<const float2*>(smraw + SM::PBUF), &mb[2], (unsigned)i & 1u, P, &fail);
     else
-      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), xb, lut,
+      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), tw, lut,
                                     reinterpret_cast<float2*>(smraw + SM::TWR));
   }
 }

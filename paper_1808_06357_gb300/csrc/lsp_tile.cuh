@@ -129,13 +129,30 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void bfly(T* v)
   }
 }
 
-template <typename T> struct Swz;
-template <> struct Swz<float2> {   // 16 x 8 B per 128 B bank row
+// Exchange-buffer swizzles: XOR the position within a 128-byte bank row with higher
+// index bits so that the threads of a warp hit distinct banks.  SW = 0 is the
+// swizzle of every line geometry below; SW = 1..3 are complex64 swizzles for column
+// lines of 256 threads (consecutive threads on adjacent columns), chosen per line
+// length by a bank model of every exchange pattern (conflict-free for 2^4..2^11
+// points, where SW = 0 costs up to 1.5x the minimum wavefronts at 2^10).
+template <typename T, int SW = 0> struct Swz;
+template <> struct Swz<float2, 0> {   // 16 x 8 B per 128 B bank row
   static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 4) & 15); }
 };
-template <> struct Swz<double2> {  // 8 x 16 B per 128 B bank row
+template <> struct Swz<float2, 1> {
+  static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 2) & 15); }
+};
+template <> struct Swz<float2, 2> {
+  static __device__ __forceinline__ int f(int e) { return e ^ (((e >> 2) ^ (e >> 3)) & 15); }
+};
+template <> struct Swz<float2, 3> {
+  static __device__ __forceinline__ int f(int e) { return e ^ (((e >> 2) ^ (e >> 1)) & 15); }
+};
+template <> struct Swz<double2, 0> {  // 8 x 16 B per 128 B bank row
   static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 3) & 7); }
 };
+// SW for a complex64 column line of 2^LOGL points on 256 threads
+constexpr int col_swizzle(int logl) { return logl == 11 ? 2 : logl == 9 ? 3 : 1; }
 
 // State and phase-table loads and state stores bypass L1 (each point is touched
 // once per sweep) but stay in L2 with normal priority: when state and tables fit
@@ -150,7 +167,7 @@ template <typename T> __device__ __forceinline__ T ldtab(const T* p) { return __
 // ---------------------------------------------------------------------------
 // NW independent workers of NT threads share a CTA; each transforms its own
 // tile and synchronises on its own named barrier (id 1 + worker).
-template <typename T, int NT, int LOGL, bool MAJOR, int NW = 1>
+template <typename T, int NT, int LOGL, bool MAJOR, int NW = 1, int SW = 0>
 struct Line {
   static constexpr int L = 1 << LOGL;
   static __device__ __forceinline__ int tid() { return NW == 1 ? (int)threadIdx.x : (int)(threadIdx.x & (NT - 1)); }
@@ -191,7 +208,7 @@ struct Line {
     else { b = beta & (C - 1); j = beta >> LOGC; }
   }
   static __device__ __forceinline__ int sidx(int b, int i) {
-    return Swz<T>::f(MAJOR ? (b << LOGL) + i : (i << LOGC) + b);
+    return Swz<T, SW>::f(MAJOR ? (b << LOGL) + i : (i << LOGC) + b);
   }
 
   // ---- forward pass S: registers hold inputs x[j + r L/R] ----
@@ -297,43 +314,6 @@ struct Line {
       for (int i = 0; i < 16; ++i) v[i] = w[i];
     }
   }
-  // The same transforms with the exchanges alternating between two buffers a, b:
-  // exchange k of a call goes through buffer (PAR + k) & 1, so a buffer is written
-  // again only two exchanges after it was read, with a barrier in between, and each
-  // exchange needs one barrier instead of two.  The caller guarantees that no thread
-  // still reads the buffer of the call's first exchange; a call that follows another
-  // within a tile continues the alternation (PAR = parity after the previous call).
-  static constexpr int NX = P - 1;                     // exchanges of one transform
-  template <int PAR, int S = 1>
-  static __device__ __forceinline__ void dft2(T* a, T* b, const T* tw, T (&v)[16]) {
-    if constexpr (S > 1) read_in<S>(((PAR + S - 2) & 1) ? b : a, v);
-    fwd_body<S>(tw, v);
-    if constexpr (S < P) {
-      write_out<S>(((PAR + S - 1) & 1) ? b : a, v);
-      sync();
-      dft2<PAR, S + 1>(a, b, tw, v);
-    } else {
-      constexpr int R = 1 << radix_log(S);
-      T w[16];
-#pragma unroll
-      for (int q = 0; q < 16 / R; ++q)
-#pragma unroll
-        for (int t = 0; t < R; ++t) w[q * R + t] = v[q * R + out_at<R>(t)];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = w[i];
-    }
-  }
-  template <int PAR, int S = P>
-  static __device__ __forceinline__ void idft2(T* a, T* b, const T* tw, T (&v)[16]) {
-    if constexpr (S < P) read_out<S>(((PAR + P - S - 1) & 1) ? b : a, v);
-    inv_body<S>(tw, v);
-    if constexpr (S > 1) {
-      write_in<S>(((PAR + P - S) & 1) ? b : a, v);
-      sync();
-      idft2<PAR, S - 1>(a, b, tw, v);
-    }
-  }
-
   // Inverse line DFT (unnormalised): registers holding the last forward
   // pass' outputs in natural order -> the pass-1 input pattern.
   template <int S = P>
