@@ -243,10 +243,11 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
 
 /*
  * lsp_plan_schedule -- the plan's execution path and kernel schedule.  Path 4 has
- * three schedules: 0 two CTAs per SM, one exchange buffer, potential-phase tiles
- * brought in by TMA; 1 two CTAs per SM, two exchange buffers (one barrier per
- * radix pass), P read directly; 2 three CTAs per SM, one exchange buffer, P read
- * directly.  Other paths have one schedule (0).  Not in the paper.
+ * three schedules, all with two CTAs per SM and potential-phase tiles brought in
+ * by TMA: 0 line twiddles read where they are used; 1 each radix pass' twiddles
+ * loaded before the barriers that precede the pass; 2 as 1 with the column
+ * lines' twiddles in shared memory.  Other paths have one schedule (0).  Not in
+ * the paper.
  *   path, sched  receive the values (either may be NULL).  Errors: BAD_ARG.
  * lsp_plan_set_schedule -- choose a schedule of the current path (results are
  * the same to rounding).  Errors: BAD_ARG, UNSUPPORTED.

@@ -20,7 +20,7 @@
 // between, and a tail column sweep (inverse half, P_half): 2 N + 1 launches,
 // replayed as a graph.
 //
-// Each CTA (256 threads, 16 points each, two or three CTAs per SM) walks its tiles with
+// Each CTA (256 threads, 16 points each, two CTAs per SM) walks its tiles with
 // the next tile's copy in flight: column tiles are 2-D tensor copies (boxes of
 // C columns x up to 256 rows, one tensor map per array), row tiles one 32 KiB
 // bulk copy, the K byte index a 4 KiB bulk copy into the same slot.  A slot
@@ -70,17 +70,18 @@ enum S2Kind { kS2Head = 0, kS2Mid, kS2Tail, kS2ColFwd, kS2Row, kS2RowFwd, kS2Kin
 constexpr int kS2NT = 256, kS2Tile = 4096, kS2LogN1 = 12;
 constexpr unsigned kS2TileBytes = kS2Tile * 8u;
 
-// Schedules of the kernels (the autotuner's choice per lattice size):
-//   0: two CTAs per SM; the line twiddle tables read through L1; the potential-phase
-//      tile of the column sweeps brought in by TMA
-//   1: as 0, with the line twiddle tables copied into shared memory at the start
-//   2: three CTAs per SM (at most 80 registers a thread); P read straight from
-//      global memory after the inverse transform
+// Schedules of the kernels (the autotuner's choice per lattice size); all run two
+// CTAs per SM and bring the potential-phase tile of the column sweeps in by TMA:
+//   0: the line twiddles of each radix-16 pass read (through L1) where they are used
+//   1: each pass' twiddles loaded before the barriers and the exchange that precede
+//      the pass, so that their latency overlaps the wait
+//   2: as 1, with the column lines' twiddle table copied into shared memory
 template <int V> struct S2Sched;
-template <> struct S2Sched<0> { static constexpr int MINB = 2; static constexpr bool TWS = false, PTMA = true; };
-template <> struct S2Sched<1> { static constexpr int MINB = 2; static constexpr bool TWS = true, PTMA = true; };
-template <> struct S2Sched<2> { static constexpr int MINB = 3; static constexpr bool TWS = false, PTMA = false; };
+template <> struct S2Sched<0> { static constexpr bool PRE = false, TWS_COL = false; };
+template <> struct S2Sched<1> { static constexpr bool PRE = true, TWS_COL = false; };
+template <> struct S2Sched<2> { static constexpr bool PRE = true, TWS_COL = true; };
 static_assert(kS2NumScheds == 3, "schedule count as declared for the host");
+constexpr int kS2MinBlocks = 2;
 
 template <int M, int KIND> struct S2Geo {
   static constexpr bool COL = KIND <= kS2ColFwd;
@@ -97,20 +98,32 @@ template <int M, int KIND> struct S2Geo {
 };
 
 // Shared memory of one CTA: two tile slots (+ the K byte index of a row), the
-// potential-phase tile, the line twiddles (schedule 1), the K table per norm value,
+// potential-phase tile, the column twiddles (schedule 2), the K table per norm value,
 // the sixteen per-tile twiddles of a row.
 template <int M, int KIND, bool KIDX, int V> struct S2Smem {
   using Geo = S2Geo<M, KIND>;
-  using SC = S2Sched<V>;
+  static constexpr bool TWS = Geo::COL && S2Sched<V>::TWS_COL;
   static constexpr unsigned KIDX_BYTES = (!Geo::COL && KIDX) ? 4096u : 0u;
   static constexpr unsigned SLOT = kS2TileBytes + KIDX_BYTES;
   static constexpr unsigned PBUF = 2 * SLOT;
-  static constexpr unsigned TWS = PBUF + ((Geo::HAS_P && SC::PTMA) ? kS2TileBytes : 0u);
-  static constexpr unsigned LUT = TWS + (SC::TWS ? (unsigned)Geo::G::TW_ENTRIES * 8u : 0u);
+  static constexpr unsigned TWT = PBUF + (Geo::HAS_P ? kS2TileBytes : 0u);
+  static constexpr unsigned LUT = TWT + (TWS ? (unsigned)Geo::G::TW_ENTRIES * 8u : 0u);
   static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // W_n^{256 r xi2}, r < 16
   static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 16u * 8u);
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
 };
+
+// Forward / inverse line transform of a tile under schedule V.
+template <typename G, int V>
+__device__ __forceinline__ void s2_dft(float2* sm, const float2* tw, float2 (&v)[16]) {
+  if constexpr (S2Sched<V>::PRE) G::dft_pre(sm, tw, v);
+  else G::dft(sm, tw, v);
+}
+template <typename G, int V>
+__device__ __forceinline__ void s2_idft(float2* sm, const float2* tw, float2 (&v)[16]) {
+  if constexpr (S2Sched<V>::PRE) G::idft_pre(sm, tw, v);
+  else G::idft(sm, tw, v);
+}
 
 // Bounded wait for phase `parity` of mbarrier b: at most `limit` non-blocking polls
 // ~32 ns apart.  On expiry the error word is set and *fail raised, and the wait goes
@@ -192,10 +205,9 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
     }
   }
   __syncthreads();                                      // slot read: it becomes an exchange buffer
-  if constexpr (Geo::INV_IN) G::idft(slot, tw, v);
+  if constexpr (Geo::INV_IN) s2_idft<G, V>(slot, tw, v);
   if constexpr (Geo::HAS_P) {
-    const float2* ptab = KIND == kS2Mid ? I.Pf : I.Ph;
-    if constexpr (S2Sched<V>::PTMA) s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
+    s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
 #pragma unroll
     for (int q = 0; q < 16 / R1; ++q) {
       int b, j; G::template bm<LR1>(q, b, j);
@@ -203,14 +215,12 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
       for (int r = 0; r < R1; ++r) {
         float2 x = v[q * R1 + r];
         if constexpr (Geo::INV_IN) x = cscale(x, I.inv_n);
-        const int i = j + (r << (LOGL - LR1));
-        const float2 e = S2Sched<V>::PTMA ? pbuf[(i << LOGC) + b] : ldtab(ptab + (c0 + b) + ((size_t)i << kS2LogN1));
-        v[q * R1 + r] = apply_phase(x, e);
+        v[q * R1 + r] = apply_phase(x, pbuf[((j + (r << (LOGL - LR1))) << LOGC) + b]);
       }
     }
   }
   if constexpr (Geo::FWD) {
-    G::dft(slot, tw, v);
+    s2_dft<G, V>(slot, tw, v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) stst(I.u + (c0 + bn) + ((size_t)(jn + (q << (LOGL - 4))) << kS2LogN1), v[q]);
   } else {
@@ -256,7 +266,7 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
   const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
-  G::dft(slot, tw, v);
+  s2_dft<G, V>(slot, tw, v);
   if constexpr (KIND == kS2RowFwd) {
     const int N2 = 1 << (M - kS2LogN1);
 #pragma unroll
@@ -274,17 +284,16 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
     }
-    G::idft(slot, tw, v);
+    s2_idft<G, V>(slot, tw, v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)t << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
   }
 }
 
 template <int M, int KIND, bool KIDX, int V>
-__global__ void __launch_bounds__(kS2NT, S2Sched<V>::MINB) s2_sweep(const __grid_constant__ S2Params P) {
+__global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_constant__ S2Params P) {
   using Geo = S2Geo<M, KIND>;
   using SM = S2Smem<M, KIND, KIDX, V>;
-  constexpr bool PT = Geo::HAS_P && S2Sched<V>::PTMA;   // potential-phase tile by TMA
   extern __shared__ __align__(128) unsigned char smdyn[];
   unsigned char* smraw = smdyn + ((128u - (smem_u32(smdyn) & 127u)) & 127u);
   __shared__ __align__(8) unsigned long long mb[3];    // slot 0, slot 1, potential-phase tile
@@ -298,11 +307,11 @@ __global__ void __launch_bounds__(kS2NT, S2Sched<V>::MINB) s2_sweep(const __grid
     fence_mbar_init();
   }
   float2* lut = reinterpret_cast<float2*>(smraw + SM::LUT);
-  // line twiddles: shared-memory copy (schedule 1) or the table in global memory; every
-  // instance of a launch has the same line length, hence the same table
+  // line twiddles: shared-memory copy (schedule 2, columns) or the table in global memory;
+  // every instance of a launch has the same line length, hence the same table
   const float2* tw = Geo::COL ? P.inst[0].tw_cols : P.inst[0].tw_rows;
-  if constexpr (S2Sched<V>::TWS) {
-    float2* tws = reinterpret_cast<float2*>(smraw + SM::TWS);
+  if constexpr (SM::TWS) {
+    float2* tws = reinterpret_cast<float2*>(smraw + SM::TWT);
     for (int k = threadIdx.x; k < Geo::G::TW_ENTRIES; k += kS2NT) tws[k] = __ldg(tw + k);
     tw = tws;
   }
@@ -344,7 +353,7 @@ __global__ void __launch_bounds__(kS2NT, S2Sched<V>::MINB) s2_sweep(const __grid
         const S2Inst& In = inst_of(t + G, ln);
         s2_issue_tile<M, KIND, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
       }
-      if constexpr (PT) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+      if constexpr (Geo::HAS_P) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
     }
     if constexpr (Geo::COL)
       s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), tw,

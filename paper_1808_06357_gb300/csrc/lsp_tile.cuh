@@ -314,6 +314,95 @@ struct Line {
       for (int i = 0; i < 16; ++i) v[i] = w[i];
     }
   }
+  // Twiddles of the thread's radix-16 butterfly in pass S >= 2 (one butterfly per
+  // thread there): w[r - 1] = W_{16 Ns}^{jm r}, r = 1..15.
+  template <int S>
+  static __device__ __forceinline__ void load_tw(const T* __restrict__ tw, T (&w)[15]) {
+    static_assert(S > 1 && radix_log(S) == 4, "passes after the first are radix 16");
+    constexpr int LNS = lns(S);
+    int b, j;
+    bm<4>(0, b, j);
+    const T* tq = tw + tw_off(S) + (j & ((1 << LNS) - 1));
+#pragma unroll
+    for (int r = 1; r < 16; ++r) w[r - 1] = tq[(r - 1) << LNS];
+  }
+  // dft / idft with each pass' twiddles loaded before the barriers and the exchange
+  // that precede the pass, so that their latency overlaps the wait and the reads.
+  template <int S = 1>
+  static __device__ __forceinline__ void dft_pre(T* sm, const T* tw, T (&v)[16]) {
+    fwd_body<S>(tw, v);
+    if constexpr (S < P) {
+      T w[15];
+      load_tw<S + 1>(tw, w);
+      sync();
+      write_out<S>(sm, v);
+      sync();
+      read_in<S + 1>(sm, v);
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = twmul(v[r], w[r - 1]);
+      dft_pre_tail<S + 1>(sm, tw, v);
+    } else {
+      constexpr int R = 1 << radix_log(S);
+      T o[16];
+#pragma unroll
+      for (int q = 0; q < 16 / R; ++q)
+#pragma unroll
+        for (int t = 0; t < R; ++t) o[q * R + t] = v[q * R + out_at<R>(t)];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = o[i];
+    }
+  }
+  // pass S >= 2 of dft_pre after its twiddles: the butterfly, then as dft_pre
+  template <int S>
+  static __device__ __forceinline__ void dft_pre_tail(T* sm, const T* tw, T (&v)[16]) {
+    bfly<16, -1>(v);
+    if constexpr (S < P) {
+      T w[15];
+      load_tw<S + 1>(tw, w);
+      sync();
+      write_out<S>(sm, v);
+      sync();
+      read_in<S + 1>(sm, v);
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = twmul(v[r], w[r - 1]);
+      dft_pre_tail<S + 1>(sm, tw, v);
+    } else {
+      T o[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) o[t] = v[out_at<16>(t)];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = o[i];
+    }
+  }
+  template <int S = P>
+  static __device__ __forceinline__ void idft_pre(T* sm, const T* tw, T (&v)[16]) {
+    if constexpr (S > 1) {
+      T w[15];
+      load_tw<S>(tw, w);
+      if constexpr (S < P) {
+        sync();
+        read_out<S>(sm, v);
+      }
+      T o[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) o[t] = v[t];
+      bfly<16, +1>(o);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = o[out_at<16>(r)];
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = twmulc(v[r], w[r - 1]);
+      sync();
+      write_in<S>(sm, v);
+      idft_pre<S - 1>(sm, tw, v);
+    } else {
+      if constexpr (S < P) {
+        sync();
+        read_out<S>(sm, v);
+      }
+      inv_body<S>(tw, v);
+    }
+  }
+
   // Inverse line DFT (unnormalised): registers holding the last forward
   // pass' outputs in natural order -> the pass-1 input pattern.
   template <int S = P>
