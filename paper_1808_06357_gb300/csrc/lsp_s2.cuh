@@ -108,8 +108,8 @@ template <int M, int KIND, bool KIDX, int V> struct S2Smem {
   static constexpr unsigned PBUF = 2 * SLOT;
   static constexpr unsigned TWT = PBUF + (Geo::HAS_P ? kS2TileBytes : 0u);
   static constexpr unsigned LUT = TWT + (TWS ? (unsigned)Geo::G::TW_ENTRIES * 8u : 0u);
-  static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // W_n^{256 r xi2}, r < 16
-  static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 16u * 8u);
+  static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // 2 x W_n^{256 r xi2}, r < 16
+  static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 2u * 16u * 8u);
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
 };
 
@@ -204,7 +204,7 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
       for (int r = 0; r < R1; ++r) v[q * R1 + r] = slot[((j + (r << (LOGL - LR1))) << LOGC) + b];
     }
   }
-  __syncthreads();                                      // slot read: it becomes an exchange buffer
+  // the slot becomes the exchange buffer: the transform's first barrier precedes its first write
   if constexpr (Geo::INV_IN) s2_idft<G, V>(slot, tw, v);
   if constexpr (Geo::HAS_P) {
     s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
@@ -236,9 +236,16 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
 
 // One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
 // after the state in the slot, thread-major (thread jn's 16 bytes, q = 0..15, together).
+// W_n^{256 r t}, r < 16, of row t into twr (threads 0..15).
+template <int M>
+__device__ __forceinline__ void s2_row_twr(const S2Inst& I, int t, float2* twr) {
+  if (threadIdx.x < 16)
+    twr[threadIdx.x] = s2_wn<M>(I, ((unsigned)t * (threadIdx.x << (kS2LogN1 - 4))) & ((1u << M) - 1u));
+}
+
 template <int M, int KIND, bool KIDX, int V>
 __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* lut,
-                                            float2* twr) {
+                                            const float2* twr) {
   using Geo = S2Geo<M, KIND>;
   using G = typename Geo::G;
   constexpr int LOGL = kS2LogN1;
@@ -250,7 +257,6 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
   // pass-1 pattern: register r holds k1 = j + 256 r of row t (j = jn here: one line per tile)
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = slot[jn + (r << (LOGL - 4))];
-  if (threadIdx.x < 16) twr[threadIdx.x] = s2_wn<M>(I, ((unsigned)t * (threadIdx.x << (LOGL - 4))) & NMASK);
   uint4 kb = make_uint4(0, 0, 0, 0);
   float2 kv[(KIND == kS2Row && !KIDX) ? 16 : 1];
   if constexpr (KIND == kS2Row) {
@@ -261,8 +267,8 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
       for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + ((size_t)t << LOGL) + jn + (q << (LOGL - 4)));
     }
   }
-  __syncthreads();                                      // slot read: it becomes an exchange buffer
-  // four-step twiddle W_n^{k1 t} = W_n^{j t} W_n^{256 r t}
+  // the slot becomes the exchange buffer: the transform's first barrier precedes its first write
+  // four-step twiddle W_n^{k1 t} = W_n^{j t} W_n^{256 r t} (twr written before the tile's barrier)
   const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
@@ -326,12 +332,14 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
       for (int k = threadIdx.x; k < P.inst[0].nlut; k += kS2NT) lut[k] = P.inst[0].klut[k];
   }
   __syncthreads();
+  float2* twr = reinterpret_cast<float2*>(smraw + SM::TWR);   // row sweeps: per-tile twiddles, by tile parity
   int t = (int)blockIdx.x;
   if (t >= P.ntiles) return;
-  if (threadIdx.x == 0) {
+  {
     int l;
     const S2Inst& I0 = inst_of(t, l);
-    s2_issue_tile<M, KIND, KIDX>(I0, l, smraw, &mb[0]);
+    if (threadIdx.x == 0) s2_issue_tile<M, KIND, KIDX>(I0, l, smraw, &mb[0]);
+    if constexpr (!Geo::COL) s2_row_twr<M>(I0, l, twr);
   }
   for (int i = 0; t < P.ntiles; ++i, t += G) {
     const int s = i & 1;
@@ -347,20 +355,21 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
     }
     __syncthreads();                                    // tile i - 1 done; the wait above ended in every thread
     if (*(volatile int*)&fail) break;                   // no copy is in flight here
-    if (threadIdx.x == 0) {
-      if (t + G < P.ntiles) {
-        int ln;
-        const S2Inst& In = inst_of(t + G, ln);
-        s2_issue_tile<M, KIND, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
-      }
-      if constexpr (Geo::HAS_P) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+    if (t + G < P.ntiles) {
+      int ln;
+      const S2Inst& In = inst_of(t + G, ln);
+      if (threadIdx.x == 0) s2_issue_tile<M, KIND, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
+      // the next row's twiddles: the buffer of parity i + 1 was last read in tile i - 1
+      if constexpr (!Geo::COL) s2_row_twr<M>(In, ln, twr + 16 * (s ^ 1));
+    }
+    if constexpr (Geo::HAS_P) {
+      if (threadIdx.x == 0) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
     }
     if constexpr (Geo::COL)
       s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), tw,
                               reinterpret_cast<const float2*>(smraw + SM::PBUF), &mb[2], (unsigned)i & 1u, P, &fail);
     else
-      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), tw, lut,
-                                    reinterpret_cast<float2*>(smraw + SM::TWR));
+      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), tw, lut, twr + 16 * s);
   }
 }
 
