@@ -87,7 +87,8 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
- * 0, 3, 1, 4, but for complex64 1, 3, 0, 4 at n = 2^13 and 3, 0, 1, 4 from n = 2^20;
+ * 0, 3, 1, 4, but for complex64 1, 3, 0, 4 at n = 2^13, 4, 3, 0, 1 from 2^20 to
+ * 2^23 and 3, 0, 1, 4 above;
  * rank 2: 1, 2; reported by lsp_plan_info, changed by lsp_plan_set_path or
  * lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
@@ -97,7 +98,7 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
  *     (10, 8), (11, 9), (12, 10), (14, 12);
  *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25};
- *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 20 <= m <= 23.
+ *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 16 <= m <= 23.
  * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
@@ -268,7 +269,10 @@ int lsp_autotune_cache(int clear, int64_t* entries);
  * Batched stepping: many independent instances (same precision and device)
  * advanced together.  Instances on the SMEM-resident path run one CTA each:
  * one launch per power-of-two size on the register-resident line kernel and
- * one for all others; rank-1 two-sweep instances are grouped by lattice size,
+ * one for all others; instances on path 4 (rank 1, 2^16 .. 2^23 points, any mix
+ * of sizes, step sizes and K forms) advance together, one launch per sweep over
+ * all their tiles, replayed as a CUDA graph for calls of 16 steps or more;
+ * rank-1 two-sweep instances are grouped by lattice size,
  * one persistent cooperative launch per size per call; rank-1 four-sweep
  * instances of up to 2^22 points are grouped by size, one launch per sweep over
  * all the group's tiles, replayed as a CUDA graph for calls of 16 steps or more;

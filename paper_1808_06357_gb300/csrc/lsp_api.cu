@@ -647,15 +647,21 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   // complex64 at 2^13 points: the SMEM-resident line kernel (15 batched instances, 500
   // steps: 4.6 ms against 8.4 ms for the two-sweep kernel)
   const int logn0 = ilog2exact(ntot);
+  // complex64 from 2^20 to 2^23 points: the TMA-fed two-sweep path measured faster than both
+  // (G point-steps/s, 100-step calls: 61.6 against 42.1 at 2^20, 68.6 against 55.1 at 2^22,
+  // 57.2 against 54.0 at 2^23)
   const bool four_first = prec == LSP_C64 && logn0 >= 20;
+  const bool tma_first = prec == LSP_C64 && logn0 >= 20 && logn0 <= 23;
   const bool small_first = prec == LSP_C64 && r == 1 && logn0 == 13;
-  const int order1[] = {small_first ? kPathSmall : four_first ? kPathRank1x4 : kPathMultipass,
-                        four_first ? kPathMultipass : kPathRank1x4, small_first ? kPathMultipass : kPathSmall,
-                        kPathRank1x2};
+  const int order_tma[] = {kPathRank1x2, kPathRank1x4, kPathMultipass, kPathSmall};
+  const int order_rest[] = {small_first ? kPathSmall : four_first ? kPathRank1x4 : kPathMultipass,
+                            four_first ? kPathMultipass : kPathRank1x4, small_first ? kPathMultipass : kPathSmall,
+                            kPathRank1x2};
+  const int* order1 = tma_first ? order_tma : order_rest;
   const int order2[] = {kPathSmall, kPathRank2};
   int path = -1;
   if (r == 1) {
-    for (int c : order1) if (path < 0 && path_available(p, c)) path = c;
+    for (int k = 0; k < 4; ++k) if (path < 0 && path_available(p, order1[k])) path = order1[k];
   } else {
     for (int c : order2) if (path < 0 && path_available(p, c)) path = c;
   }

@@ -39,6 +39,7 @@ void free_batch(lsp_batch b) {
     cudaFree(c.rowmap);
   }
   for (auto& c : b->s4classes) s4_class_free(c);
+  s2_group_free(b->s2group);
   if (b->s4_graph) cudaGraphExecDestroy(b->s4_graph);
   if (b->capture) cudaStreamDestroy(b->capture);
   cudaFree(b->bar);
@@ -112,6 +113,7 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
   std::map<std::pair<int, bool>, std::vector<int>> by_m4;
   for (int i = 0; i < count; ++i) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
+    else if (s2_batchable(plans[i])) b->s2group.ids.push_back(i);
     else if (s4_batchable(plans[i])) by_m4[{plans[i]->logn, plans[i]->kidx != nullptr}].push_back(i);
     else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4 || plans[i]->path == kPathRank1x2)
       b->seq_ids.push_back(i);
@@ -127,6 +129,10 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
     bool changed = false;
     if (!rc) rc = s4_class_sync(c, b->plans, &changed, nullptr);
     if (!rc && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = LSP_ERR_CUDA;
+    if (rc) return fail(rc);
+  }
+  if (!b->s2group.ids.empty()) {
+    int rc = s2_group_init(b->s2group, b->plans);
     if (rc) return fail(rc);
   }
   // SMEM-resident groups
@@ -198,6 +204,10 @@ int lsp_batch_steps(lsp_batch b, const double* dt, int64_t nsteps, void* stream)
   }
   if (!b->s4classes.empty()) {
     int rc = s4_batch_steps(b, nsteps, s);
+    if (rc) return rc;
+  }
+  if (!b->s2group.ids.empty()) {
+    int rc = s2_group_steps(b->s2group, b->plans, nsteps, b->err, s);
     if (rc) return rc;
   }
   for (int i : b->seq_ids) {     // each fills the GPU by itself

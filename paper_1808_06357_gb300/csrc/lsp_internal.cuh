@@ -121,7 +121,7 @@ struct lsp_plan_s {
   void* desc = nullptr;       // device copies of the multipass kernel descriptors
   void* s2desc = nullptr;     // TMA two-sweep path: descriptors (state, spectral copy, other buffer)
   std::vector<unsigned char> s2host0;   // host copy of descriptor slot 0
-  int s2_sched = 0;                     // kernel schedule of the TMA two-sweep path (autotuned)
+  int s2_sched = 1;                     // kernel schedule of the TMA two-sweep path (autotuned)
   int* err_host = nullptr;    // pinned mirror of the device error word
   unsigned* bar = nullptr;    // grid-barrier counter
   int* err = nullptr;         // device error word
@@ -175,6 +175,19 @@ struct lsp_batch_s {
     int total[3] = {};
   };
   std::vector<S4Class> s4classes;
+  // rank-1 instances on the TMA two-sweep path (2^16 .. 2^23 points, any mix of sizes):
+  // one launch per sweep over all their tiles, replayed as a CUDA graph
+  struct S2Group {
+    std::vector<int> ids;
+    void* inst = nullptr;                   // device array of descriptors
+    std::vector<unsigned char> inst_host;   // its host copy
+    int2* map = nullptr;                    // launch tile -> (instance in group, local tile)
+    int total = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<unsigned char> graph_key;
+    cudaStream_t capture = nullptr;
+  };
+  S2Group s2group;
   cudaGraphExec_t s4_graph = nullptr;       // the four-sweep classes' launches of one call
   std::vector<unsigned char> s4_graph_key;
   cudaStream_t capture = nullptr;
@@ -364,6 +377,11 @@ int s2_upload_desc(lsp_plan p);                            // after the tables o
 int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 int s2_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
 int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms);
+bool s2_batchable(lsp_plan p);
+int s2_group_init(lsp_batch_s::S2Group& g, const std::vector<lsp_plan>& plans);
+int s2_group_steps(lsp_batch_s::S2Group& g, const std::vector<lsp_plan>& plans, int64_t nsteps, int* err,
+                   cudaStream_t s);
+void s2_group_free(lsp_batch_s::S2Group& g);
 // steps of the plan's current path on a state buffer of the plan's geometry
 int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 

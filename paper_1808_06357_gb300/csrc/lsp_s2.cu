@@ -13,8 +13,12 @@
 
 namespace lsp {
 
-constexpr int kS2MinLog = 20, kS2MaxLog = 23;
+constexpr int kS2MinLog = 16, kS2MaxLog = 23;
 
+bool s2_kernels_16(int v, S2Kernels* k);
+bool s2_kernels_17(int v, S2Kernels* k);
+bool s2_kernels_18(int v, S2Kernels* k);
+bool s2_kernels_19(int v, S2Kernels* k);
 bool s2_kernels_20(int v, S2Kernels* k);
 bool s2_kernels_21(int v, S2Kernels* k);
 bool s2_kernels_22(int v, S2Kernels* k);
@@ -22,6 +26,10 @@ bool s2_kernels_23(int v, S2Kernels* k);
 
 bool s2_kernels_for(int m, int v, S2Kernels* k) {
   switch (m) {
+    case 16: return s2_kernels_16(v, k);
+    case 17: return s2_kernels_17(v, k);
+    case 18: return s2_kernels_18(v, k);
+    case 19: return s2_kernels_19(v, k);
     case 20: return s2_kernels_20(v, k);
     case 21: return s2_kernels_21(v, k);
     case 22: return s2_kernels_22(v, k);
@@ -82,6 +90,7 @@ static int s2_inst(lsp_plan p, void* state, double2* spec, S2Inst* I) {
   I->spec = spec;
   I->nlut = p->klut ? (int)p->max_norm2 + 1 : 0;
   I->inv_n = (float)(1.0 / (double)p->ntot);
+  I->m = p->logn;
   return LSP_OK;
 }
 
@@ -263,6 +272,95 @@ int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, doub
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   return rc;
+}
+
+}  // namespace lsp
+
+// --------------------------------------------------------------------------
+// Batches: every path-4 instance (2^16 .. 2^23 points, mixed sizes) in one launch per sweep
+// --------------------------------------------------------------------------
+namespace lsp {
+
+bool s2_batchable(lsp_plan p) {
+  return p->path == kPathRank1x2 && p->logn >= kS2BatchMinLog && p->logn <= kS2BatchMaxLog;
+}
+
+int s2_group_init(lsp_batch_s::S2Group& g, const std::vector<lsp_plan>& plans) {
+  std::vector<int2> map;
+  for (size_t k = 0; k < g.ids.size(); ++k) {
+    const int nt = 1 << (plans[g.ids[k]]->logn - kS2LogN1);
+    for (int t = 0; t < nt; ++t) map.push_back(make_int2((int)k, t));
+  }
+  g.total = (int)map.size();
+  if (cudaMalloc(&g.map, map.size() * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&g.inst, g.ids.size() * sizeof(S2Inst)) != cudaSuccess) { cudaGetLastError(); return LSP_ERR_OOM; }
+  LSP_CUDA_TRY(cudaMemcpy(g.map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  // kernel attributes and grids, outside any capture
+  const S2BatchKernels K = s2_batch_kernels();
+  int grid = 0;
+  for (int k = 0; k < kS2Kinds; ++k) {
+    if (!K.k[k]) continue;
+    int rc = s2_grid(K.k[k], K.smem[k], &grid);
+    if (rc) return rc;
+  }
+  return LSP_OK;
+}
+
+void s2_group_free(lsp_batch_s::S2Group& g) {
+  cudaFree(g.inst);
+  cudaFree(g.map);
+  if (g.graph) cudaGraphExecDestroy(g.graph);
+  if (g.capture) cudaStreamDestroy(g.capture);
+  g = lsp_batch_s::S2Group();
+}
+
+static int s2_group_launches(const lsp_batch_s::S2Group& g, int64_t nsteps, int* err, cudaStream_t s) {
+  const S2BatchKernels K = s2_batch_kernels();
+  const S2Inst* d = (const S2Inst*)g.inst;
+  auto go = [&](int kind) { return s2_launch(K.k[kind], K.smem[kind], d, g.map, g.total, err, kSpinLimit, s); };
+  int rc = go(kS2Head);
+  for (int64_t st = 0; st < nsteps && !rc; ++st) {
+    rc = go(kS2Row);
+    if (!rc) rc = go(st + 1 < nsteps ? kS2Mid : kS2Tail);
+  }
+  return rc;
+}
+
+// nsteps steps of every instance of the group; descriptors are refreshed (stream-ordered)
+// when a plan's tables or state buffer moved, and calls of 16 steps or more replay a graph.
+int s2_group_steps(lsp_batch_s::S2Group& g, const std::vector<lsp_plan>& plans, int64_t nsteps, int* err,
+                   cudaStream_t s) {
+  std::vector<unsigned char> h(g.ids.size() * sizeof(S2Inst));
+  for (size_t k = 0; k < g.ids.size(); ++k) {
+    lsp_plan p = plans[g.ids[k]];
+    S2Inst I;
+    int rc = s2_inst(p, p->u, nullptr, &I);
+    if (rc) return rc;
+    memcpy(h.data() + k * sizeof(S2Inst), &I, sizeof(I));
+  }
+  if (h != g.inst_host) {
+    LSP_CUDA_TRY(cudaMemcpyAsync(g.inst, h.data(), h.size(), cudaMemcpyHostToDevice, s));
+    g.inst_host = h;
+  }
+  if (nsteps < kS2GraphMinSteps) return s2_group_launches(g, nsteps, err, s);
+  std::vector<unsigned char> key(sizeof(nsteps) + sizeof(err));
+  memcpy(key.data(), &nsteps, sizeof(nsteps));
+  memcpy(key.data() + sizeof(nsteps), &err, sizeof(err));
+  if (!g.graph || key != g.graph_key) {
+    if (g.graph) { cudaGraphExecDestroy(g.graph); g.graph = nullptr; }
+    if (!g.capture) LSP_CUDA_TRY(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
+    LSP_CUDA_TRY(cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal));
+    const int rc = s2_group_launches(g, nsteps, err, g.capture);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g.capture, &gr);
+    if (rc || ec != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return rc ? rc : LSP_ERR_CUDA; }
+    const cudaError_t ei = cudaGraphInstantiate(&g.graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ei != cudaSuccess) { g.graph = nullptr; return LSP_ERR_CUDA; }
+    g.graph_key = key;
+  }
+  LSP_CUDA_TRY(cudaGraphLaunch(g.graph, s));
+  return LSP_OK;
 }
 
 }  // namespace lsp

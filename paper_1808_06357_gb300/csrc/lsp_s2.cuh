@@ -55,6 +55,7 @@ struct S2Inst {                 // 128-byte aligned through its tensor maps
   double2* spec;             // spectral output (chi order)
   int nlut;
   float inv_n;
+  int m;                     // log2 n
 };
 
 struct S2Params {
@@ -142,34 +143,39 @@ __device__ __forceinline__ void s2_wait(unsigned long long* b, unsigned parity, 
   }
 }
 
-// Issue the copies of local tile t of instance I into slot `dst` (thread 0 only).
-template <int M, int KIND, bool KIDX>
-__device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
-  using Geo = S2Geo<M, KIND>;
+// Column tile t of an n = 2^m array (tensor map `map`): C = 2^(24 - m) columns, boxes of
+// min(N2, 256) rows, into dst (thread 0 only).
+__device__ __forceinline__ void s2_issue_cols(const CUtensorMap* map, int m, int t, unsigned char* dst,
+                                              unsigned long long* b) {
+  const int ln2 = m - kS2LogN1;
+  const int c = 1 << (kS2LogN1 - ln2);
+  const int br = (1 << ln2) < 256 ? (1 << ln2) : 256;
+  const int nb = (1 << ln2) / br;
   fence_proxy_async();
-  if constexpr (Geo::COL) {
-    mbar_arrive_expect_tx(b, kS2TileBytes);
-    constexpr int NB = (1 << Geo::LN2) / Geo::BR;
-#pragma unroll
-    for (int k = 0; k < NB; ++k)
-      tma_load_2d(dst + (size_t)k * Geo::BR * Geo::C * 8, &I.tu, t * Geo::C, k * Geo::BR, b);
+  mbar_arrive_expect_tx(b, kS2TileBytes);
+  for (int k = 0; k < nb; ++k) tma_load_2d(dst + (size_t)k * br * c * 8, map, t * c, k * br, b);
+}
+
+// Issue the copies of local tile t of instance I into slot `dst` (thread 0 only): a column
+// tile, or a row with its K byte index when the instance has one and the slot has room
+// for it (KIDX).
+template <bool COL, bool KIDX>
+__device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
+  if constexpr (COL) {
+    s2_issue_cols(&I.tu, I.m, t, dst, b);
   } else {
-    mbar_arrive_expect_tx(b, kS2TileBytes + (KIDX ? 4096u : 0u));
+    const bool kx = KIDX && I.kidx != nullptr;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(b, kS2TileBytes + (kx ? 4096u : 0u));
     bulk_g2s(dst, I.u + ((size_t)t << kS2LogN1), kS2TileBytes, b);
-    if constexpr (KIDX) bulk_g2s(dst + kS2TileBytes, I.kidx + ((size_t)t << kS2LogN1), 4096u, b);
+    if (kx) bulk_g2s(dst + kS2TileBytes, I.kidx + ((size_t)t << kS2LogN1), 4096u, b);
   }
 }
 
 // The potential-phase tile (same geometry as the state's column tile).
-template <int M, int KIND>
+template <int KIND>
 __device__ __forceinline__ void s2_issue_p(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
-  using Geo = S2Geo<M, KIND>;
-  const CUtensorMap* map = KIND == kS2Mid ? &I.tpf : &I.tph;
-  fence_proxy_async();
-  mbar_arrive_expect_tx(b, kS2TileBytes);
-  constexpr int NB = (1 << Geo::LN2) / Geo::BR;
-#pragma unroll
-  for (int k = 0; k < NB; ++k) tma_load_2d(dst + (size_t)k * Geo::BR * Geo::C * 8, map, t * Geo::C, k * Geo::BR, b);
+  s2_issue_cols(KIND == kS2Mid ? &I.tpf : &I.tph, I.m, t, dst, b);
 }
 
 // W_n^a (a < n) from the two-level table: W_N1^{a >> LN2} W_n^{a mod N2}.
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
   {
     int l;
     const S2Inst& I0 = inst_of(t, l);
-    if (threadIdx.x == 0) s2_issue_tile<M, KIND, KIDX>(I0, l, smraw, &mb[0]);
+    if (threadIdx.x == 0) s2_issue_tile<Geo::COL, KIDX>(I0, l, smraw, &mb[0]);
     if constexpr (!Geo::COL) s2_row_twr<M>(I0, l, twr);
   }
   for (int i = 0; t < P.ntiles; ++i, t += G) {
@@ -358,12 +364,12 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
     if (t + G < P.ntiles) {
       int ln;
       const S2Inst& In = inst_of(t + G, ln);
-      if (threadIdx.x == 0) s2_issue_tile<M, KIND, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
+      if (threadIdx.x == 0) s2_issue_tile<Geo::COL, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
       // the next row's twiddles: the buffer of parity i + 1 was last read in tile i - 1
       if constexpr (!Geo::COL) s2_row_twr<M>(In, ln, twr + 16 * (s ^ 1));
     }
     if constexpr (Geo::HAS_P) {
-      if (threadIdx.x == 0) s2_issue_p<M, KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+      if (threadIdx.x == 0) s2_issue_p<KIND>(I, l, smraw + SM::PBUF, &mb[2]);
     }
     if constexpr (Geo::COL)
       s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), tw,
@@ -413,5 +419,128 @@ template <int M> bool s2_kernels_m(int v, S2Kernels* k) {
 
 // Defined by the instantiation units (one per lattice size); false for other sizes.
 bool s2_kernels_for(int m, int v, S2Kernels* k);
+
+// ---------------------------------------------------------------------------
+// Batches of instances of uneven size: one launch per sweep kind covers every tile
+// of every instance with 2^16 <= n <= 2^23 points (tiles of 4096 points in all of
+// them); a tile's instance fixes its geometry (column length, twiddle tables, K form,
+// step size through its tables), dispatched per tile.  Schedule 1 (twiddles loaded
+// ahead of the barriers), two CTAs per SM, slots sized for the K byte index.
+// ---------------------------------------------------------------------------
+constexpr int kS2BatchMinLog = 16, kS2BatchMaxLog = 23;
+constexpr int kS2BatchSched = 1;
+
+// Shared memory of a batch CTA: two slots (rows: with room for the K byte index), the
+// potential-phase tile, two K tables and two sets of row twiddles (by tile parity).
+template <int KIND> struct S2BatchSmem {
+  static constexpr bool COL = KIND <= kS2ColFwd;
+  static constexpr bool HAS_P = KIND == kS2Head || KIND == kS2Mid || KIND == kS2Tail;
+  static constexpr unsigned SLOT = kS2TileBytes + (COL ? 0u : 4096u);
+  static constexpr unsigned PBUF = 2 * SLOT;
+  static constexpr unsigned LUT = PBUF + (HAS_P ? kS2TileBytes : 0u);
+  static constexpr unsigned TWR = LUT + (COL ? 0u : 2u * 256u * 8u);
+  static constexpr unsigned USED = TWR + (COL ? 0u : 2u * 16u * 8u);
+  static constexpr unsigned BYTES = USED + 128u;
+};
+
+template <int KIND, int MM = kS2BatchMinLog>
+__device__ __forceinline__ void s2_batch_tile(const S2Inst& I, int l, unsigned char* slot, unsigned char* smraw,
+                                              float2* lut, const float2* twr, unsigned long long* mbp,
+                                              unsigned pparity, const S2Params& P, int* fail) {
+  if constexpr (MM <= kS2BatchMaxLog) {
+    if (I.m != MM) {
+      s2_batch_tile<KIND, MM + 1>(I, l, slot, smraw, lut, twr, mbp, pparity, P, fail);
+      return;
+    }
+    using Geo = S2Geo<MM, KIND>;
+    using SM = S2BatchSmem<KIND>;
+    if constexpr (Geo::COL) {
+      s2_col_tile<MM, KIND, kS2BatchSched>(I, l, reinterpret_cast<float2*>(slot), I.tw_cols,
+                                           reinterpret_cast<const float2*>(smraw + SM::PBUF), mbp, pparity, P, fail);
+    } else if (I.kidx) {
+      s2_row_tile<MM, KIND, true, kS2BatchSched>(I, l, reinterpret_cast<float2*>(slot), I.tw_rows, lut, twr);
+    } else {
+      s2_row_tile<MM, KIND, false, kS2BatchSched>(I, l, reinterpret_cast<float2*>(slot), I.tw_rows, lut, twr);
+    }
+  }
+}
+
+// Row twiddles W_n^{256 r t} of a tile of any batch size.
+template <int MM = kS2BatchMinLog>
+__device__ __forceinline__ void s2_batch_twr(const S2Inst& I, int l, float2* twr) {
+  if constexpr (MM <= kS2BatchMaxLog) {
+    if (I.m != MM) s2_batch_twr<MM + 1>(I, l, twr);
+    else s2_row_twr<MM>(I, l, twr);
+  }
+}
+
+// K table of instance I into lut (all threads; nlut <= 256 when the instance has a byte index).
+__device__ __forceinline__ void s2_batch_lut(const S2Inst& I, float2* lut) {
+  if (I.kidx)
+    for (int k = threadIdx.x; k < I.nlut; k += kS2NT) lut[k] = I.klut[k];
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_batch_sweep(const __grid_constant__ S2Params P) {
+  using SM = S2BatchSmem<KIND>;
+  constexpr bool COL = SM::COL;
+  extern __shared__ __align__(128) unsigned char smdyn[];
+  unsigned char* smraw = smdyn + ((128u - (smem_u32(smdyn) & 127u)) & 127u);
+  __shared__ __align__(8) unsigned long long mb[3];    // slot 0, slot 1, potential-phase tile
+  __shared__ int fail;
+  const int G = (int)gridDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&mb[0], 1);
+    mbar_init(&mb[1], 1);
+    mbar_init(&mb[2], 1);
+    fail = 0;
+    fence_mbar_init();
+  }
+  // rows: the K table and the per-row twiddles of tile i sit in buffer i & 1, written for
+  // tile i + 1 while tile i runs (the buffer of parity i + 1 was last read in tile i - 1)
+  float2* lut = reinterpret_cast<float2*>(smraw + SM::LUT);
+  float2* twr = reinterpret_cast<float2*>(smraw + SM::TWR);
+  int t = (int)blockIdx.x;
+  if (t < P.ntiles) {
+    const int2 m0 = P.map[t];
+    const S2Inst& I0 = P.inst[m0.x];
+    if (threadIdx.x == 0) s2_issue_tile<COL, !COL>(I0, m0.y, smraw, &mb[0]);
+    if constexpr (!COL) {
+      s2_batch_twr(I0, m0.y, twr);
+      s2_batch_lut(I0, lut);
+    }
+  }
+  __syncthreads();
+  if (t >= P.ntiles) return;
+  for (int i = 0; t < P.ntiles; ++i, t += G) {
+    const int s = i & 1;
+    unsigned char* slot = smraw + (size_t)s * SM::SLOT;
+    s2_wait(&mb[s], (unsigned)(i >> 1) & 1u, P.spin_limit, P.err, &fail);
+    const int2 mt = P.map[t];
+    const S2Inst& I = P.inst[mt.x];
+    __syncthreads();                                    // tile i - 1 done; the wait above ended in every thread
+    if (*(volatile int*)&fail) break;                   // no copy is in flight here
+    if (t + G < P.ntiles) {
+      const int2 mn = P.map[t + G];
+      const S2Inst& In = P.inst[mn.x];
+      if (threadIdx.x == 0) s2_issue_tile<COL, !COL>(In, mn.y, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
+      if constexpr (!COL) {
+        s2_batch_twr(In, mn.y, twr + 16 * (s ^ 1));
+        s2_batch_lut(In, lut + 256 * (s ^ 1));
+      }
+    }
+    if constexpr (SM::HAS_P) {
+      if (threadIdx.x == 0) s2_issue_p<KIND>(I, mt.y, smraw + SM::PBUF, &mb[2]);
+    }
+    s2_batch_tile<KIND>(I, mt.y, slot, smraw, lut + 256 * s, twr + 16 * s, &mb[2], (unsigned)i & 1u, P, &fail);
+  }
+}
+
+// Batch kernels by sweep kind (kS2Row reads K through the byte index where an instance has one).
+struct S2BatchKernels {
+  const void* k[kS2Kinds] = {};
+  size_t smem[kS2Kinds] = {};
+};
+S2BatchKernels s2_batch_kernels();
 
 }  // namespace lsp

@@ -86,7 +86,7 @@ def test_four_sweep_spectral(lib):
 def test_paths_set_path_and_errors(lib):
     inst = w.c2(20)
     plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64")
-    assert plan.info()["path"] == lib.PATH_RANK1_4SWEEP         # complex64 default from 2^20
+    assert plan.info()["path"] == lib.PATH_RANK1_TMA            # complex64 default from 2^20 to 2^23
     assert lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128").info()["path"] == lib.PATH_MULTIPASS
     assert set(plan.paths()) == {lib.PATH_MULTIPASS, lib.PATH_RANK1_4SWEEP, lib.PATH_RANK1_TMA}
     c128 = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128")
@@ -114,7 +114,7 @@ def test_autotune_keeps_results_and_state(lib):
     v, u0 = inst.v(P), inst.u0(P)
     plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c128")
     assert plan.info()["path"] == lib.PATH_MULTIPASS           # complex128 default at 2^22
-    assert lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64").info()["path"] == lib.PATH_RANK1_4SWEEP
+    assert lib.Plan(inst.Zmat, inst.n, inst.gamma, prec="c64").info()["path"] == lib.PATH_RANK1_TMA
     plan.set_potential(torch.from_numpy(v).cuda())
     plan.set_state(torch.from_numpy(u0).cuda())
     chosen, ms = plan.autotune(inst.dt, 10)

@@ -33,7 +33,7 @@ def _plan(lib, inst, prec="c64"):
     return plan, v, u0
 
 
-@pytest.mark.parametrize("m,nsteps", [(20, 20), (21, 7), (22, 17), (23, 3)])
+@pytest.mark.parametrize("m,nsteps", [(16, 20), (17, 5), (18, 17), (19, 4), (20, 20), (21, 7), (22, 17), (23, 3)])
 def test_tma_two_sweep_matches_oracle(lib, m, nsteps):
     """Every sweep kind of the path (head, row with the byte-index K, mid, tail), plain launches
     below 16 steps and the replayed graph from 16 on, against the oracle's steps."""
@@ -161,3 +161,37 @@ def test_tma_two_sweep_adjoint_autotune_and_batch(lib):
     assert lib.PATH_RANK1_TMA in ms and path in ms
     assert _rel(plan.get_state(prec="c128").cpu().numpy(), ref) < TOL64
     plan.destroy()
+
+
+def test_batch_of_uneven_sizes_in_one_launch_per_sweep(lib):
+    """Path-4 instances of 2^16 .. 2^20 points (d = 3..8, each with its own lattice, potential and
+    step size) advance together: one launch per sweep over all their tiles, graph-replayed for
+    20-step calls and launched directly for 5; every instance ends where it ends when stepped
+    alone (same arithmetic), and one instance of every size is checked against the oracle."""
+    import torch
+    pool = w.c3()
+    insts = []
+    for m in range(16, 21):
+        insts += [i for i in pool if i.npoints == 1 << m][:2]
+    plans, singles, refs = [], [], []
+    for inst in insts:
+        for lst in (plans, singles):
+            p, v, u0 = _plan(lib, inst)
+            lst.append(p)
+        refs.append((v, u0))
+    assert all(p.info()["max_norm2"] < 256 for p in plans)
+    batch = lib.Batch(plans)
+    dts = [inst.dt for inst in insts]
+    for n in (20, 5, 20):
+        batch.steps(dts, n)
+        for q, dt in zip(singles, dts):
+            q.strang_steps(dt, n)
+    assert batch.status() == 0
+    for p, q, inst in zip(plans, singles, insts):
+        assert torch.equal(p.get_state(), q.get_state()), inst.name
+    for k in range(0, len(insts), 2):
+        inst, (v, u0) = insts[k], refs[k]
+        norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+        ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 45)
+        assert _rel(plans[k].get_state(prec="c128").cpu().numpy(), ref) < TOL64, inst.name
+    batch.destroy()
