@@ -179,7 +179,8 @@ def test_batch_of_uneven_sizes_in_one_launch_per_sweep(lib):
             p, v, u0 = _plan(lib, inst)
             lst.append(p)
         refs.append((v, u0))
-    assert all(p.info()["max_norm2"] < 256 for p in plans)
+    kidx = [p.info()["max_norm2"] < 256 for p in plans]
+    assert any(kidx) and not all(kidx), kidx                  # K by byte index and from the table
     batch = lib.Batch(plans)
     dts = [inst.dt for inst in insts]
     for n in (20, 5, 20):
