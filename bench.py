@@ -424,8 +424,8 @@ def run_ours(args):
         sw = plan.sweep_times(inst.dt, 64, stream=stream)
         k_bytes = 24.0 * n
         which = "P" if sw["P"] >= sw["K"] else "K"
-        name = ("s2 column sweep (conj W_n, IDFT_N2, 1/n, P, DFT_N2, W_n; TMA tensor tiles)" if which == "P" else
-                "s2 row sweep (DFT_4096, K by byte index, IDFT_4096; TMA bulk tiles)")
+        name = ("s2 column sweep (IDFT_N2, 1/n, P, DFT_N2; TMA tensor tiles)" if which == "P" else
+                "s2 row sweep (W_n, DFT_4096, K by byte index, IDFT_4096, conj W_n; TMA bulk tiles)")
         rec = traffic_record(f"c64_n2p{args.log2n}_tma", "s2") if STEPS_PER_CALL == 1000 else None
         k_traffic = rec.get("per_launch", {}).get(which) if rec else None
         step_traffic = rec.get("bytes_per_call_1000_steps") if rec else None

@@ -375,7 +375,9 @@ int lsp_cbc_reconstructing(const int32_t* I, int64_t m, int d, int r, const int6
 /*
  * lsp_sweep_times -- per-sweep durations of the multi-launch paths (2, 3, 4):
  * nsteps (2 .. 4096) Strang steps of size dt on a scratch copy of the state,
- * once untimed, then again as plain launches with a CUDA event after each;
+ * once untimed, then again with a CUDA event after each launch (path 4: the
+ * launches and events captured into a CUDA graph and replayed, as a call of 16
+ * steps or more runs; paths 2 and 3: plain launches);
  * ms[0..3] (host) = mean duration in ms of the P sweep between steps (rows /
  * X / the column sweep of path 4), the A / Y sweep, the K sweep (B / Z / the
  * row sweep of path 4) and the A^-1 / Y^-1 sweep (-1 where a path has none).

@@ -240,23 +240,48 @@ int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, doub
   for (auto& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
   std::vector<int> kind;                    // 0 mid column sweep, 2 row sweep, -1 head / tail
-  size_t k = 0;
-  auto rec = [&]() { return cudaEventRecord(ev[k++], s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; };
-  if (!rc) rc = rec();
-  if (!rc) rc = s2_launch(K.k[kS2Head], K.smem[kS2Head], d, nullptr, K.ntiles, p->err, p->spin_limit, s);
-  kind.push_back(-1);
-  if (!rc) rc = rec();
-  for (int64_t st = 0; st < nsteps && !rc; ++st) {
-    rc = s2_launch(row, row_smem, d, nullptr, K.ntiles, p->err, p->spin_limit, s);
-    kind.push_back(2);
-    if (!rc) rc = rec();
-    const bool last = st + 1 == nsteps;
-    if (!rc) rc = s2_launch(K.k[last ? kS2Tail : kS2Mid], K.smem[last ? kS2Tail : kS2Mid], d, nullptr, K.ntiles,
-                            p->err, p->spin_limit, s);
-    kind.push_back(last ? -1 : 0);
-    if (!rc) rc = rec();
+  // The launches with an event after each, captured into a CUDA graph (events as event-record
+  // nodes) and replayed, so that the sweeps follow one another as in a graph-replayed call.
+  auto issue = [&](cudaStream_t st, unsigned flags) {
+    size_t k = 0;
+    kind.clear();
+    auto rec = [&]() { return cudaEventRecordWithFlags(ev[k++], st, flags) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; };
+    int r = rec();
+    if (!r) r = s2_launch(K.k[kS2Head], K.smem[kS2Head], d, nullptr, K.ntiles, p->err, p->spin_limit, st);
+    kind.push_back(-1);
+    if (!r) r = rec();
+    for (int64_t step = 0; step < nsteps && !r; ++step) {
+      r = s2_launch(row, row_smem, d, nullptr, K.ntiles, p->err, p->spin_limit, st);
+      kind.push_back(2);
+      if (!r) r = rec();
+      const bool last = step + 1 == nsteps;
+      if (!r) r = s2_launch(K.k[last ? kS2Tail : kS2Mid], K.smem[last ? kS2Tail : kS2Mid], d, nullptr, K.ntiles,
+                            p->err, p->spin_limit, st);
+      kind.push_back(last ? -1 : 0);
+      if (!r) r = rec();
+    }
+    return r;
+  };
+  cudaGraphExec_t exec = nullptr;
+  if (!rc) {
+    cudaStream_t cap = nullptr;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int r = issue(cap, cudaEventRecordExternal);
+      ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && r == LSP_OK &&
+           cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (cap) cudaStreamDestroy(cap);
+    if (!ok) {                                           // no event nodes: plain launches
+      cudaGetLastError();
+      if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+    }
   }
-  if (!rc && cudaEventSynchronize(ev[k - 1]) != cudaSuccess) rc = LSP_ERR_CUDA;
+  if (!rc) rc = exec ? (cudaGraphLaunch(exec, s) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA) : issue(s, cudaEventRecordDefault);
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = LSP_ERR_CUDA;
   if (!rc) {
     double sum[4] = {0, 0, 0, 0};
     int cnt[4] = {0, 0, 0, 0};
@@ -269,6 +294,7 @@ int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, doub
     }
     for (int c = 0; c < 4; ++c) ms[c] = cnt[c] ? sum[c] / cnt[c] : -1.0;
   }
+  if (exec) cudaGraphExecDestroy(exec);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   return rc;
