@@ -153,6 +153,14 @@ template <> struct Swz<double2, 0> {  // 8 x 16 B per 128 B bank row
 };
 // SW for a complex64 column line of 2^LOGL points on 256 threads
 constexpr int col_swizzle(int logl) { return logl == 11 ? 2 : logl == 9 ? 3 : 1; }
+// Each swizzle changes only bits 0..3 (float2; 0..2 for double2) as a function of the bits
+// below its granule: f(e + OFF) = f(e) + OFF for every OFF that is a multiple of the granule.
+template <typename T, int SW> struct SwzGranule;
+template <> struct SwzGranule<float2, 0> { static constexpr int G = 256; };   // bits 4..7
+template <> struct SwzGranule<float2, 1> { static constexpr int G = 64; };    // bits 2..5
+template <> struct SwzGranule<float2, 2> { static constexpr int G = 128; };   // bits 2..6
+template <> struct SwzGranule<float2, 3> { static constexpr int G = 64; };    // bits 1..5
+template <> struct SwzGranule<double2, 0> { static constexpr int G = 64; };   // bits 3..5
 
 // State and phase-table loads and state stores bypass L1 (each point is touched
 // once per sweep) but stay in L2 with normal priority: when state and tables fit
@@ -210,6 +218,14 @@ struct Line {
   static __device__ __forceinline__ int sidx(int b, int i) {
     return Swz<T, SW>::f(MAJOR ? (b << LOGL) + i : (i << LOGC) + b);
   }
+  // swizzled position of element (b, i0 + DI) for a compile-time DI: one swizzle of the
+  // thread's base position plus an immediate when DI's offset is a multiple of the granule
+  template <int DI>
+  static __device__ __forceinline__ int sidx_at(int b, int i0) {
+    constexpr int OFF = MAJOR ? DI : DI << LOGC;
+    if constexpr (OFF % SwzGranule<T, SW>::G == 0) return sidx(b, i0) + OFF;
+    else return sidx(b, i0 + DI);
+  }
 
   // ---- forward pass S: registers hold inputs x[j + r L/R] ----
   template <int S>
@@ -226,6 +242,18 @@ struct Line {
       bfly<R, -1>(&v[q * R]);
     }
   }
+  // element index t * STEP of a butterfly (t < R) at base i0, as compile-time offsets
+  template <int STEP, int R, typename F>
+  static __device__ __forceinline__ void for_offsets(int b, int i0, F&& f) {
+    for_offsets_impl<STEP, R, 0>(b, i0, f);
+  }
+  template <int STEP, int R, int K, typename F>
+  static __device__ __forceinline__ void for_offsets_impl(int b, int i0, F& f) {
+    if constexpr (K < R) {
+      f(K, sidx_at<K * STEP>(b, i0));
+      for_offsets_impl<STEP, R, K + 1>(b, i0, f);
+    }
+  }
   template <int S>
   static __device__ __forceinline__ void write_out(T* sm, const T (&v)[16]) {
     constexpr int LR = radix_log(S), R = 1 << LR, LNS = lns(S);
@@ -233,8 +261,7 @@ struct Line {
     for (int q = 0; q < 16 / R; ++q) {
       int b, j; bm<LR>(q, b, j);
       const int ob = ((j >> LNS) << (LNS + LR)) + (j & ((1 << LNS) - 1));
-#pragma unroll
-      for (int t = 0; t < R; ++t) sm[sidx(b, ob + (t << LNS))] = v[q * R + out_at<R>(t)];
+      for_offsets<(1 << LNS), R>(b, ob, [&](int t, int pos) { sm[pos] = v[q * R + out_at<R>(t)]; });
     }
   }
   template <int S>
@@ -243,8 +270,7 @@ struct Line {
 #pragma unroll
     for (int q = 0; q < 16 / R; ++q) {
       int b, j; bm<LR>(q, b, j);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = sm[sidx(b, j + (r << (LOGL - LR)))];
+      for_offsets<(1 << (LOGL - LR)), R>(b, j, [&](int r, int pos) { v[q * R + r] = sm[pos]; });
     }
   }
   // ---- inverse pass S (conjugate transpose of forward pass S) ----
@@ -255,8 +281,7 @@ struct Line {
     for (int q = 0; q < 16 / R; ++q) {
       int b, j; bm<LR>(q, b, j);
       const int ob = ((j >> LNS) << (LNS + LR)) + (j & ((1 << LNS) - 1));
-#pragma unroll
-      for (int t = 0; t < R; ++t) v[q * R + t] = sm[sidx(b, ob + (t << LNS))];
+      for_offsets<(1 << LNS), R>(b, ob, [&](int t, int pos) { v[q * R + t] = sm[pos]; });
     }
   }
   template <int S>
@@ -284,8 +309,7 @@ struct Line {
 #pragma unroll
     for (int q = 0; q < 16 / R; ++q) {
       int b, j; bm<LR>(q, b, j);
-#pragma unroll
-      for (int r = 0; r < R; ++r) sm[sidx(b, j + (r << (LOGL - LR)))] = v[q * R + r];
+      for_offsets<(1 << (LOGL - LR)), R>(b, j, [&](int r, int pos) { sm[pos] = v[q * R + r]; });
     }
   }
 
