@@ -156,9 +156,16 @@ __global__ void build_klut(T* lut, int count, double turns_k) {
 
 // Bin chi held at position i of the K sweep's native order (identity for the SMEM path).
 __device__ __forceinline__ long long native_bin(long long i, int order, int logN1, int logN2) {
-  if (order == kPathMultipass || order == kPathRank1x2) {   // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
+  if (order == kPathMultipass) {   // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
     long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
     return xi2 + (xi1 << logN2);
+  }
+  if (order == kPathRank1x2) {
+    // position j + 256 q + N1 xi2 (N1 = 4096) <- bin xi2 + N2 xi1 with xi1 = j3 + 256 q: thread
+    // j = 32 w + 16 h + c of the row transform ends with bins j3 = 16 c + 2 w + h
+    const long long j = i & 255, q = (i >> 8) & 15, xi2 = i >> logN1;
+    const long long j3 = ((j & 15) << 4) | ((j >> 5) << 1) | ((j >> 4) & 1);
+    return xi2 + ((j3 + (q << 8)) << logN2);
   }
   if (order == kPathRank2) {
     // n1 = A B (A = 2^ceil(m1/2)): position (e + A g) n2 + xi2 <- bin (g + B e) n2 + xi2
@@ -177,13 +184,29 @@ __device__ __forceinline__ long long native_bin(long long i, int order, int logN
   return i;
 }
 
+// The point whose potential phase sits at position i of the TMA two-sweep path's P tables:
+// column tile T = i / 4096 (columns k1 = T C .. T C + C - 1, C = 4096 / N2) in the order of
+// the column transform's threads.  Position 16 j + 2 x + h of a tile is value s = 2 (x ^ (j & 7)) + h
+// of thread j (16-byte pairs XOR-swizzled so that eight threads' pair loads hit distinct
+// banks); value s = q R1 + r is element i2 = (beta >> LOGC) + r N2 / R1 of column
+// T C + (beta & (C - 1)), beta = j + 256 q, with R1 the radix of the column's first pass.
+__host__ __device__ __forceinline__ long long s2_p_point(long long i, int logN2) {
+  const int lr1 = logN2 % 4 == 0 ? 4 : logN2 % 4, logc = 12 - logN2;
+  const long long tile = i >> 12, w = i & 4095, j = w >> 4;
+  const long long s = 2 * (((w >> 1) & 7) ^ (j & 7)) + (w & 1);
+  const long long q = s >> lr1, r = s & ((1 << lr1) - 1), beta = j + 256 * q;
+  const long long b = beta & ((1 << logc) - 1), i2 = (beta >> logc) + (r << (logN2 - lr1));
+  return (i2 << 12) + (tile << logc) + b;
+}
+
 // K (skipped when K == nullptr: the kernels then take K from klut through kidx)
 template <typename T>
 __global__ void build_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf, T* K,
                              const T* __restrict__ klut, long long n, double turns_v, double turns_k, int order,
                              int logN1, int logN2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double th = v[i] * turns_v;                       // -dt v / (4 pi gamma): half step, in turns
+    const long long pk = order == kPathRank1x2 ? s2_p_point(i, logN2) : i;
+    double th = v[pk] * turns_v;                      // -dt v / (4 pi gamma): half step, in turns
     T a, b, c;
     encode_phase_pair(th, &a, &b);
     Ph[i] = a;
@@ -199,7 +222,7 @@ __global__ void build_tables(const double* __restrict__ v, const int32_t* __rest
 
 // ||h||^2 of the bin at each native position, as a byte (four-sweep paths, max ||h||^2 < 256).
 // TMA two-sweep path: thread-major within each row of N1 = 4096 positions, so that a thread's
-// 16 bytes are adjacent: position 16 j + q of row xi2 holds xi1 = j + 256 q.
+// 16 bytes are adjacent: byte 16 j + q of a row belongs to native position j + 256 q.
 __global__ void build_kidx(const int32_t* __restrict__ norm2, uint8_t* kidx, long long n, int order, int logN1,
                            int logN2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -473,6 +496,14 @@ static int setup_path_tables(lsp_plan p, int path) {
     tw.clear();
     passes(tw, p->logN1);
     p->twr_entries = (int)(tw.size() / sz);
+    {
+      // the row's pass-3 part [r-1][jm] (jm = 16 t + e < 256) stored [r-1][e][t]: the order in
+      // which a warp of the row transform reads it
+      std::vector<unsigned char> t3(tw.begin() + 240 * sz, tw.end());
+      for (int r = 0; r < 15; ++r)
+        for (int jm = 0; jm < 256; ++jm)
+          memcpy(tw.data() + (240 + r * 256 + (jm & 15) * 16 + (jm >> 4)) * sz, t3.data() + (r * 256 + jm) * sz, sz);
+    }
     passes(tw, p->logN2);
     if ((rc = upload(p, &p->tw_pass, tw))) return rc;
     return s2_upload_desc(p);

@@ -73,9 +73,7 @@ static int encode_cols(CUtensorMap* map, const void* base, int m) {
 
 static int s2_inst(lsp_plan p, void* state, double2* spec, S2Inst* I) {
   memset(I, 0, sizeof(*I));
-  int rc = encode_cols(&I->tu, state, p->logn);
-  if (!rc) rc = encode_cols(&I->tph, p->Ph, p->logn);
-  if (!rc) rc = encode_cols(&I->tpf, p->Pf, p->logn);
+  const int rc = encode_cols(&I->tu, state, p->logn);
   if (rc) return rc;
   I->u = (float2*)state;
   I->Ph = (const float2*)p->Ph;

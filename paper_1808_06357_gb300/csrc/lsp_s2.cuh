@@ -10,8 +10,9 @@
 //   column sweep (tile: C = 4096 / N2 adjacent columns k1):
 //       IDFT_N2, 1/n, P, DFT_N2
 //   row sweep (tile: one row xi2):  W_n^{k1 xi2}, DFT_N1, K, IDFT_N1, conj W_n^{k1 xi2}
-// with K in the row sweep's native order (position xi1 + N1 xi2 holds bin
-// xi2 + N2 xi1).  The four-step twiddle sits in the row sweep, where the row
+// with K in the row sweep's native order (row xi2 of the table holds the bins
+// xi2 + N2 xi1 in the order in which the row transform's threads hold them, S2Row
+// below).  The four-step twiddle sits in the row sweep, where the row
 // xi2 is fixed: thread j holds k1 = j + 256 r (r = 0..15), so
 //   W_n^{k1 xi2} = W_n^{j xi2} W_n^{256 r xi2},
 // one table value per thread and sixteen per tile (shared memory) instead of a
@@ -21,9 +22,11 @@
 // replayed as a graph.
 //
 // Each CTA (256 threads, 16 points each, two CTAs per SM) walks its tiles with
-// the next tile's copy in flight: column tiles are 2-D tensor copies (boxes of
-// C columns x up to 256 rows, one tensor map per array), row tiles one 32 KiB
-// bulk copy, the K byte index a 4 KiB bulk copy into the same slot.  A slot
+// the next tile's copy in flight: column tiles of the state are 2-D tensor copies
+// (boxes of C columns x up to 256 rows), row tiles one 32 KiB bulk copy, the K byte
+// index a 4 KiB bulk copy into the same slot.  The potential-phase tables are stored
+// tile by tile in the order in which the column transform's threads use them, so a
+// column tile's phases are one 32 KiB bulk copy too.  A slot
 // that has been read into registers serves as the tile's exchange buffer for
 // the radix-16 passes, so two slots (and one potential-phase buffer for the
 // column sweeps, whose copy is issued at the start of the tile and consumed
@@ -40,12 +43,11 @@ namespace lsp {
 // Per-instance descriptor in device memory.
 struct S2Inst {                 // 128-byte aligned through its tensor maps
   CUtensorMap tu;            // state as {N1 (inner), N2} of 8-byte elements, box {C, BR}
-  CUtensorMap tph;           // P_half, same geometry
-  CUtensorMap tpf;           // P_full, same geometry
   float2* u;
-  const float2* Ph;          // P_half, P_full in point order (schedules that load P directly)
-  const float2* Pf;
-  const float2* K;           // K in the row sweep's native order (when kidx is null)
+  const float2* Ph;          // P_half, P_full: 4096 values per column tile, in the order of the
+  const float2* Pf;          // column transform's threads (16 per thread, 16-byte pairs swizzled)
+  const float2* K;           // K in the row sweep's native order (when kidx is null): row xi2,
+                             // position j + 256 q holds the bin of thread j's forward output q
   const uint8_t* kidx;       // ||h||^2 per row position, thread-major within a row (max < 256)
   const float2* klut;        // K per value of ||h||^2
   const float2* tw_rows;     // per-pass twiddles of the 4096-point rows
@@ -114,6 +116,104 @@ template <int M, int KIND, bool KIDX, int V> struct S2Smem {
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
 };
 
+// 4096-point row transform (radix 16, 16, 16) with one block-wide exchange per
+// direction.  Butterfly j of pass s reads x[j + 256 r] and writes
+// y[(j / Ns) 16 Ns + j mod Ns + Ns t] (Ns = 1, 16, 256), as the Line passes do; what
+// differs is which thread runs which butterfly, and the exchange layouts.  Pass 2's
+// butterfly 16 c + e writes positions 256 c + 16 t + e, which are read by pass 3's
+// butterflies 16 t + e only: the pass-2 -> pass-3 exchange joins butterflies of one e.
+// So warp w runs e in {2w, 2w + 1} with c (pass 2) or t (pass 3) = lane mod 16, and that
+// exchange never leaves the 512 buffer positions the warp read after pass 1; __syncwarp
+// orders it.  Pass 1 keeps butterfly j = thread (the tile's coalesced input and output
+// pattern).  Layouts, conflict-free for every access of a warp:
+//   pass 1 -> 2: y at y ^ ((y >> 4) & 15)
+//   pass 2 -> 3: element (c, t, e) at 256 c + 16 (c ^ t) + (e ^ c ^ t)
+// Twiddles: pass 2's W_256^{e r} from the row table's [r-1][jm] part; pass 3's
+// W_4096^{(16 t + e) r} stored [r-1][e][t] (the host's row table permutes that part),
+// so that a warp's 32 loads of one r are contiguous.
+struct S2Row {
+  static constexpr int kTw3 = 15 * 16;                  // start of pass 3's table
+  static __device__ __forceinline__ int e_of() {
+    return (int)(((threadIdx.x >> 5) << 1) | ((threadIdx.x >> 4) & 1u));
+  }
+  static __device__ __forceinline__ int c_of() { return (int)(threadIdx.x & 15u); }
+  // pass-3 butterfly of this thread: the forward's output t is bin xi1 = jn3() + 256 t
+  static __device__ __forceinline__ int jn3() { return (c_of() << 4) | e_of(); }
+  static __device__ __forceinline__ void load_tw2(const float2* __restrict__ tw, int e, float2 (&w)[15]) {
+#pragma unroll
+    for (int r = 1; r < 16; ++r) w[r - 1] = tw[((r - 1) << 4) + e];
+  }
+  static __device__ __forceinline__ void load_tw3(const float2* __restrict__ tw, int e, int c, float2 (&w)[15]) {
+    const float2* tq = tw + kTw3 + (e << 4) + c;
+#pragma unroll
+    for (int r = 1; r < 16; ++r) w[r - 1] = tq[(r - 1) << 8];
+  }
+  template <int DIR> static __device__ __forceinline__ void butterfly(float2 (&v)[16]) {
+    float2 o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = v[i];
+    bfly<16, DIR>(o);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = o[out_at<16>(t)];
+  }
+
+  // v[r] = x[j + 256 r] (j = thread)  ->  v[t] = X[jn3() + 256 t]
+  static __device__ __forceinline__ void fwd(float2* sm, const float2* __restrict__ tw, float2 (&v)[16]) {
+    const int j = (int)threadIdx.x, c = c_of(), e = e_of();
+    const int a2 = (c << 4) | (e ^ c), b2 = (c << 8) | a2;
+    float2 w[15];
+    load_tw2(tw, e, w);
+    butterfly<-1>(v);
+    __syncthreads();                                    // every thread has read its tile input
+#pragma unroll
+    for (int t = 0; t < 16; ++t) sm[(j << 4) | (t ^ (j & 15))] = v[t];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = sm[(r << 8) + a2];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = twmul(v[r], w[r - 1]);
+    load_tw3(tw, e, c, w);
+    butterfly<-1>(v);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) sm[b2 ^ (17 * t)] = v[t];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = sm[a2 ^ (273 * r)];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = twmul(v[r], w[r - 1]);
+    butterfly<-1>(v);
+  }
+
+  // v[t] = X[jn3() + 256 t]  ->  v[r] = unnormalised inverse DFT at x[j + 256 r]
+  static __device__ __forceinline__ void inv(float2* sm, const float2* __restrict__ tw, float2 (&v)[16]) {
+    const int j = (int)threadIdx.x, c = c_of(), e = e_of();
+    const int a2 = (c << 4) | (e ^ c), b2 = (c << 8) | a2;
+    float2 w[15];
+    load_tw3(tw, e, c, w);
+    butterfly<+1>(v);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = twmulc(v[r], w[r - 1]);
+    load_tw2(tw, e, w);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[a2 ^ (273 * r)] = v[r];
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = sm[b2 ^ (17 * t)];
+    butterfly<+1>(v);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = twmulc(v[r], w[r - 1]);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[(r << 8) + a2] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = sm[(j << 4) | (t ^ (j & 15))];
+    butterfly<+1>(v);
+  }
+};
+
 // Forward / inverse line transform of a tile under schedule V.
 template <typename G, int V>
 __device__ __forceinline__ void s2_dft(float2* sm, const float2* tw, float2 (&v)[16]) {
@@ -172,10 +272,12 @@ __device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned c
   }
 }
 
-// The potential-phase tile (same geometry as the state's column tile).
+// The potential-phase tile of column tile t: 32 KiB, contiguous in the tables' tile order.
 template <int KIND>
 __device__ __forceinline__ void s2_issue_p(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
-  s2_issue_cols(KIND == kS2Mid ? &I.tpf : &I.tph, I.m, t, dst, b);
+  fence_proxy_async();
+  mbar_arrive_expect_tx(b, kS2TileBytes);
+  bulk_g2s(dst, (KIND == kS2Mid ? I.Pf : I.Ph) + ((size_t)t << kS2LogN1), kS2TileBytes, b);
 }
 
 // W_n^a (a < n) from the two-level table: W_N1^{a >> LN2} W_n^{a mod N2}.
@@ -186,7 +288,7 @@ __device__ __forceinline__ float2 s2_wn(const S2Inst& I, unsigned a) {
 }
 
 // One column tile: lines = columns k1 = c0 + b of N2 points; slot holds the tile row-major
-// (element (b, i) at i C + b), pbuf the potential-phase tile in the same layout (schedule 0).
+// (element (b, i) at i C + b), pbuf the potential-phase tile in its threads' order.
 template <int M, int KIND, int V>
 __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* pbuf,
                                             unsigned long long* mbp, unsigned pparity, const S2Params& P,
@@ -213,16 +315,16 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
   // the slot becomes the exchange buffer: the transform's first barrier precedes its first write
   if constexpr (Geo::INV_IN) s2_idft<G, V>(slot, tw, v);
   if constexpr (Geo::HAS_P) {
+    // this thread's 16 phases (register order) as eight 16-byte pairs, pair x at x ^ (thread mod 8)
     s2_wait(mbp, pparity, P.spin_limit, P.err, fail);
+    const float4* pp = reinterpret_cast<const float4*>(pbuf) + 8 * threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < 16 / R1; ++q) {
-      int b, j; G::template bm<LR1>(q, b, j);
-#pragma unroll
-      for (int r = 0; r < R1; ++r) {
-        float2 x = v[q * R1 + r];
-        if constexpr (Geo::INV_IN) x = cscale(x, I.inv_n);
-        v[q * R1 + r] = apply_phase(x, pbuf[((j + (r << (LOGL - LR1))) << LOGC) + b]);
-      }
+    for (int x = 0; x < 8; ++x) {
+      const float4 pr = pp[x ^ (threadIdx.x & 7u)];
+      float2 a = v[2 * x], c = v[2 * x + 1];
+      if constexpr (Geo::INV_IN) { a = cscale(a, I.inv_n); c = cscale(c, I.inv_n); }
+      v[2 * x] = apply_phase(a, make_float2(pr.x, pr.y));
+      v[2 * x + 1] = apply_phase(c, make_float2(pr.z, pr.w));
     }
   }
   if constexpr (Geo::FWD) {
@@ -241,7 +343,8 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
 }
 
 // One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
-// after the state in the slot, thread-major (thread jn's 16 bytes, q = 0..15, together).
+// after the state in the slot, thread-major (thread jn's 16 bytes, for its forward outputs
+// q = 0..15, together).
 // W_n^{256 r t}, r < 16, of row t into twr (threads 0..15).
 template <int M>
 __device__ __forceinline__ void s2_row_twr(const S2Inst& I, int t, float2* twr) {
@@ -252,15 +355,11 @@ __device__ __forceinline__ void s2_row_twr(const S2Inst& I, int t, float2* twr) 
 template <int M, int KIND, bool KIDX, int V>
 __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* lut,
                                             const float2* twr) {
-  using Geo = S2Geo<M, KIND>;
-  using G = typename Geo::G;
   constexpr int LOGL = kS2LogN1;
-  static_assert(G::R1 == 16 && G::C == 1, "rows of 4096 points: one radix-16 butterfly per thread in pass 1");
   constexpr unsigned NMASK = (1u << M) - 1u;
   float2 v[16];
-  int bn, jn;
-  G::template bm<4>(0, bn, jn);
-  // pass-1 pattern: register r holds k1 = j + 256 r of row t (j = jn here: one line per tile)
+  const int jn = (int)threadIdx.x, j3 = S2Row::jn3();
+  // pass-1 pattern: register r holds k1 = jn + 256 r of row t
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = slot[jn + (r << (LOGL - 4))];
   uint4 kb = make_uint4(0, 0, 0, 0);
@@ -278,12 +377,12 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
   const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
-  s2_dft<G, V>(slot, tw, v);
+  S2Row::fwd(slot, tw, v);                              // v[q] = bin xi1 = j3 + 256 q of row t
   if constexpr (KIND == kS2RowFwd) {
     const int N2 = 1 << (M - kS2LogN1);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int xi1 = jn + (q << (LOGL - 4));
+      const int xi1 = j3 + (q << (LOGL - 4));
       const float2 x = cscale(v[q], I.inv_n);
       I.spec[t + (size_t)xi1 * N2] = make_double2((double)x.x, (double)x.y);
     }
@@ -296,7 +395,7 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
     }
-    s2_idft<G, V>(slot, tw, v);
+    S2Row::inv(slot, tw, v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)t << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
   }
