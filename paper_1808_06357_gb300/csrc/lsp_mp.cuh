@@ -124,6 +124,8 @@ template <typename T> struct Tw {
 
 enum Src { kFromGlobal = 0, kFromPre = 1 };
 
+// Bulk copies of a tile into the prefetch buffer, issued after the barrier that follows
+// the buffer's last reads (completed reads: the copies need no proxy fence before them).
 template <typename T, int NT, int M, bool COL>
 __device__ __forceinline__ void prefetch_tile(const MPInst<T>& I, int tile, T* pre, unsigned long long* mb);
 
@@ -168,7 +170,7 @@ __device__ __forceinline__ void col_pass(const MPInst<T>& I, int tile, T* sm, T*
   }
   if constexpr (FROM == kFromPre) {
     G::sync();                                           // prefetch buffer free: refill it
-    if (nxt >= 0) { fence_proxy_async(); prefetch_tile<T, NT, M, true>(*In, nxt, pre, mb); }
+    if (nxt >= 0) { prefetch_tile<T, NT, M, true>(*In, nxt, pre, mb); }
   }
   if constexpr (inv) G::idft(sm, tw.line, v);
 
@@ -233,7 +235,7 @@ __device__ __forceinline__ void row_pass(const MPInst<T>& I, int tile, T* sm, T*
   }
   if constexpr (FROM == kFromPre) {
     G::sync();
-    if (nxt >= 0) { fence_proxy_async(); prefetch_tile<T, NT, M, false>(*In, nxt, pre, mb); }
+    if (nxt >= 0) { prefetch_tile<T, NT, M, false>(*In, nxt, pre, mb); }
   }
 
   G::dft(sm, tw.line, v);
@@ -361,7 +363,6 @@ __device__ __forceinline__ bool persistent_sweep(const MPParams<T>& P, T* smem, 
   tile_of<T>(map, t, i, l);
   if (G::tid() == 0) mbar_arrive_expect_tx(mb, TILE_BYTES);
   G::sync();
-  fence_proxy_async();
   prefetch_tile<T, NT, M, COL>(P.inst[i], l, pre, mb);
   for (; t < total; t += stride) {
     if (!wait_prefetch(mb, parity, P.err, P.spin_limit)) fail[w] = 1;

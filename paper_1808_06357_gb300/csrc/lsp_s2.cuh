@@ -243,6 +243,12 @@ __device__ __forceinline__ void s2_wait(unsigned long long* b, unsigned parity, 
   }
 }
 
+// The copies below overwrite shared memory whose last ordinary accesses (the previous
+// tile's reads, and its exchange writes, each read back by other threads) completed
+// before the CTA barrier that precedes the issue; no proxy fence is needed for that
+// order (a fence here stalls the issuing warp on its own outstanding global stores, and
+// every other warp with it at the tile's next barrier).
+//
 // Column tile t of an n = 2^m array (tensor map `map`): C = 2^(24 - m) columns, boxes of
 // min(N2, 256) rows, into dst (thread 0 only).
 __device__ __forceinline__ void s2_issue_cols(const CUtensorMap* map, int m, int t, unsigned char* dst,
@@ -251,7 +257,6 @@ __device__ __forceinline__ void s2_issue_cols(const CUtensorMap* map, int m, int
   const int c = 1 << (kS2LogN1 - ln2);
   const int br = (1 << ln2) < 256 ? (1 << ln2) : 256;
   const int nb = (1 << ln2) / br;
-  fence_proxy_async();
   mbar_arrive_expect_tx(b, kS2TileBytes);
   for (int k = 0; k < nb; ++k) tma_load_2d(dst + (size_t)k * br * c * 8, map, t * c, k * br, b);
 }
@@ -265,7 +270,6 @@ __device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned c
     s2_issue_cols(&I.tu, I.m, t, dst, b);
   } else {
     const bool kx = KIDX && I.kidx != nullptr;
-    fence_proxy_async();
     mbar_arrive_expect_tx(b, kS2TileBytes + (kx ? 4096u : 0u));
     bulk_g2s(dst, I.u + ((size_t)t << kS2LogN1), kS2TileBytes, b);
     if (kx) bulk_g2s(dst + kS2TileBytes, I.kidx + ((size_t)t << kS2LogN1), 4096u, b);
@@ -275,7 +279,6 @@ __device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned c
 // The potential-phase tile of column tile t: 32 KiB, contiguous in the tables' tile order.
 template <int KIND>
 __device__ __forceinline__ void s2_issue_p(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
-  fence_proxy_async();
   mbar_arrive_expect_tx(b, kS2TileBytes);
   bulk_g2s(dst, (KIND == kS2Mid ? I.Pf : I.Ph) + ((size_t)t << kS2LogN1), kS2TileBytes, b);
 }
