@@ -1,7 +1,8 @@
 // Shared-memory barriers and bulk asynchronous copies (the TMA engine) used by
 // the multipass kernels: mbarrier set-up, arrival with an expected transaction
 // count, bounded polling, 1-D bulk copies and 2-D tensor copies global ->
-// shared, and the proxy fences that order them against ordinary accesses.
+// shared, 2-D tensor copies shared -> global with their bulk-group waits, and the
+// proxy fences that order them against ordinary accesses.
 #pragma once
 
 #include <cuda.h>
@@ -60,5 +61,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(b))
       : "memory");
 }
+
+// 2-D tensor copy shared -> global of one box (the tensor map's box at coordinates (x, y)),
+// in the issuing thread's bulk async-group.  Ordinary writes of the box by other threads
+// must precede it: fence_proxy_async_shared() in each writer, then a CTA barrier.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The issuing thread's committed bulk stores have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... and have completed their global writes.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 }  // namespace lsp

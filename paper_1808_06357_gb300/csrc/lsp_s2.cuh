@@ -30,9 +30,11 @@
 // that has been read into registers serves as the tile's exchange buffer for
 // the radix-16 passes, so two slots (and one potential-phase buffer for the
 // column sweeps, whose copy is issued at the start of the tile and consumed
-// after the inverse transform) are all the shared memory a CTA holds.  Waits
-// on the copies are bounded: on expiry the sticky error word is set and the
-// CTA leaves at the next tile boundary with no copy in flight.
+// after the inverse transform) are all the shared memory a CTA holds.  Column
+// tiles with short rows (n >= 2^21) leave through that buffer too: the result is
+// written there in the tile's layout and sent out by tensor stores.  Waits on the
+// copies are bounded: on expiry the sticky error word is set and the CTA leaves at
+// the next tile boundary with no load in flight (and its stores completed).
 #pragma once
 
 #include "lsp_async.cuh"
@@ -85,6 +87,14 @@ template <> struct S2Sched<1> { static constexpr bool PRE = true, TWS_COL = fals
 template <> struct S2Sched<2> { static constexpr bool PRE = true, TWS_COL = true; };
 static_assert(kS2NumScheds == 3, "schedule count as declared for the host");
 constexpr int kS2MinBlocks = 2;
+// Column tiles of lattices of at least 2^kS2TmaStoreMinLog points leave through tensor stores
+// (their rows are C <= 8 elements, 64 bytes or less: as plain stores every warp instruction
+// writes eight or more separate short row segments); larger tiles' rows store coalesced.
+#ifndef LSP_S2_TMASTORE_MIN
+#define LSP_S2_TMASTORE_MIN 21
+#endif
+constexpr int kS2TmaStoreMinLog = LSP_S2_TMASTORE_MIN;
+template <int M> constexpr bool s2_tma_store() { return M >= kS2TmaStoreMinLog; }
 
 template <int M, int KIND> struct S2Geo {
   static constexpr bool COL = KIND <= kS2ColFwd;
@@ -261,6 +271,18 @@ __device__ __forceinline__ void s2_issue_cols(const CUtensorMap* map, int m, int
   for (int k = 0; k < nb; ++k) tma_load_2d(dst + (size_t)k * br * c * 8, map, t * c, k * br, b);
 }
 
+// Column tile t of the state from src (the tile row-major, as the loads leave it) back to
+// global memory: tensor stores in thread 0's bulk group, after every thread's writes of src,
+// their proxy fence and a CTA barrier.
+__device__ __forceinline__ void s2_store_cols(const CUtensorMap* map, int m, int t, const unsigned char* src) {
+  const int ln2 = m - kS2LogN1;
+  const int c = 1 << (kS2LogN1 - ln2);
+  const int br = (1 << ln2) < 256 ? (1 << ln2) : 256;
+  const int nb = (1 << ln2) / br;
+  for (int k = 0; k < nb; ++k) tma_store_2d(map, t * c, k * br, src + (size_t)k * br * c * 8);
+  bulk_commit();
+}
+
 // Issue the copies of local tile t of instance I into slot `dst` (thread 0 only): a column
 // tile, or a row with its K byte index when the instance has one and the slot has room
 // for it (KIDX).
@@ -293,7 +315,7 @@ __device__ __forceinline__ float2 s2_wn(const S2Inst& I, unsigned a) {
 // One column tile: lines = columns k1 = c0 + b of N2 points; slot holds the tile row-major
 // (element (b, i) at i C + b), pbuf the potential-phase tile in its threads' order.
 template <int M, int KIND, int V>
-__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* pbuf,
+__device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot, const float2* tw, float2* pbuf,
                                             unsigned long long* mbp, unsigned pparity, const S2Params& P,
                                             int* fail) {
   using Geo = S2Geo<M, KIND>;
@@ -330,8 +352,27 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
       v[2 * x + 1] = apply_phase(c, make_float2(pr.z, pr.w));
     }
   }
-  if constexpr (Geo::FWD) {
-    s2_dft<G, V>(slot, tw, v);
+  if constexpr (Geo::FWD) s2_dft<G, V>(slot, tw, v);
+  if constexpr (Geo::HAS_P && s2_tma_store<M>()) {
+    // the result into the phase buffer, in the tile's row-major layout, then tensor stores by
+    // thread 0; the buffer is free once every thread has read its phases: after the forward
+    // transform's first barrier, or (tail sweep, one-pass lines) after a barrier of its own
+    if constexpr (!Geo::FWD || G::P == 1) __syncthreads();
+    if constexpr (Geo::FWD) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) pbuf[((jn + (q << (LOGL - 4))) << LOGC) + bn] = v[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16 / R1; ++q) {
+        int b, j; G::template bm<LR1>(q, b, j);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) pbuf[((j + (r << (LOGL - LR1))) << LOGC) + b] = v[q * R1 + r];
+      }
+    }
+    fence_proxy_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) s2_store_cols(&I.tu, I.m, t, reinterpret_cast<const unsigned char*>(pbuf));
+  } else if constexpr (Geo::FWD) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) stst(I.u + (c0 + bn) + ((size_t)(jn + (q << (LOGL - 4))) << kS2LogN1), v[q]);
   } else {
@@ -471,13 +512,19 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
       if constexpr (!Geo::COL) s2_row_twr<M>(In, ln, twr + 16 * (s ^ 1));
     }
     if constexpr (Geo::HAS_P) {
-      if (threadIdx.x == 0) s2_issue_p<KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+      if (threadIdx.x == 0) {
+        if constexpr (s2_tma_store<M>()) bulk_wait_read();   // tile i - 1's stores have read the buffer
+        s2_issue_p<KIND>(I, l, smraw + SM::PBUF, &mb[2]);
+      }
     }
     if constexpr (Geo::COL)
       s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), tw,
-                              reinterpret_cast<const float2*>(smraw + SM::PBUF), &mb[2], (unsigned)i & 1u, P, &fail);
+                              reinterpret_cast<float2*>(smraw + SM::PBUF), &mb[2], (unsigned)i & 1u, P, &fail);
     else
       s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), tw, lut, twr + 16 * s);
+  }
+  if constexpr (Geo::HAS_P && s2_tma_store<M>()) {
+    if (threadIdx.x == 0) bulk_wait_all();              // the last tile's stores, before the CTA ends
   }
 }
 
@@ -558,7 +605,7 @@ __device__ __forceinline__ void s2_batch_tile(const S2Inst& I, int l, unsigned c
     using SM = S2BatchSmem<KIND>;
     if constexpr (Geo::COL) {
       s2_col_tile<MM, KIND, kS2BatchSched>(I, l, reinterpret_cast<float2*>(slot), I.tw_cols,
-                                           reinterpret_cast<const float2*>(smraw + SM::PBUF), mbp, pparity, P, fail);
+                                           reinterpret_cast<float2*>(smraw + SM::PBUF), mbp, pparity, P, fail);
     } else if (I.kidx) {
       s2_row_tile<MM, KIND, true, kS2BatchSched>(I, l, reinterpret_cast<float2*>(slot), I.tw_rows, lut, twr);
     } else {
@@ -632,9 +679,15 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_batch_sweep(const __gr
       }
     }
     if constexpr (SM::HAS_P) {
-      if (threadIdx.x == 0) s2_issue_p<KIND>(I, mt.y, smraw + SM::PBUF, &mb[2]);
+      if (threadIdx.x == 0) {
+        bulk_wait_read();                               // tile i - 1's stores (if any) have read the buffer
+        s2_issue_p<KIND>(I, mt.y, smraw + SM::PBUF, &mb[2]);
+      }
     }
     s2_batch_tile<KIND>(I, mt.y, slot, smraw, lut + 256 * s, twr + 16 * s, &mb[2], (unsigned)i & 1u, P, &fail);
+  }
+  if constexpr (SM::HAS_P) {
+    if (threadIdx.x == 0) bulk_wait_all();              // the last tile's stores (if any), before the CTA ends
   }
 }
 
