@@ -88,7 +88,7 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
  * 0, 3, 1, 4, but for complex64 1, 3, 0, 4 at n = 2^13, 4, 3, 0, 1 from 2^20 to
- * 2^23 and 3, 0, 1, 4 above;
+ * 2^24 and 3, 0, 1, 4 above;
  * rank 2: 1, 2; reported by lsp_plan_info, changed by lsp_plan_set_path or
  * lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
@@ -98,7 +98,8 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of
  *     (10, 8), (11, 9), (12, 10), (14, 12);
  *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25};
- *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 16 <= m <= 23.
+ *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 16 <= m <= 24
+ *     (tiles of 4096 points on 256-thread CTAs; at 2^24 of 8192 points on 512 threads).
  * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
@@ -277,7 +278,7 @@ int lsp_autotune_cache(int clear, int64_t* entries);
  * instances of up to 2^22 points are grouped by size, one launch per sweep over
  * all the group's tiles, replayed as a CUDA graph for calls of 16 steps or more;
  * other four-sweep instances (rank 2, larger rank 1; each fills the device)
- * are stepped one after another.  A plan may belong to several batches, but a
+ * and path-4 instances of 2^24 points are stepped one after another.  A plan may belong to several batches, but a
  * call must not overlap another call on the same plans.
  *   lsp_batch_create  plans: `count` plan handles (host array, borrowed: the
  *                     plans must outlive the batch).  Errors: BAD_ARG, OOM, CUDA,

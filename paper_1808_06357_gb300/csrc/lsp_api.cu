@@ -185,16 +185,18 @@ __device__ __forceinline__ long long native_bin(long long i, int order, int logN
 }
 
 // The point whose potential phase sits at position i of the TMA two-sweep path's P tables:
-// column tile T = i / 4096 (columns k1 = T C .. T C + C - 1, C = 4096 / N2) in the order of
-// the column transform's threads.  Position 16 j + 2 x + h of a tile is value s = 2 (x ^ (j & 7)) + h
-// of thread j (16-byte pairs XOR-swizzled so that eight threads' pair loads hit distinct
-// banks); value s = q R1 + r is element i2 = (beta >> LOGC) + r N2 / R1 of column
-// T C + (beta & (C - 1)), beta = j + 256 q, with R1 the radix of the column's first pass.
+// column tile T = i / TILE (TILE = 4096 points on 256 threads, from N2 = 4096 on 8192 points
+// on 512 threads; columns k1 = T C .. T C + C - 1, C = TILE / N2) in the order of the column
+// transform's threads.  Position 16 j + 2 x + h of a tile is value s = 2 (x ^ (j & 7)) + h of
+// thread j (16-byte pairs XOR-swizzled so that eight threads' pair loads hit distinct banks);
+// value s = q R1 + r is element i2 = (beta >> LOGC) + r N2 / R1 of column T C + (beta & (C - 1)),
+// beta = j + NT q, with R1 the radix of the column's first pass.
 __host__ __device__ __forceinline__ long long s2_p_point(long long i, int logN2) {
-  const int lr1 = logN2 % 4 == 0 ? 4 : logN2 % 4, logc = 12 - logN2;
-  const long long tile = i >> 12, w = i & 4095, j = w >> 4;
+  const int lt = logN2 >= 12 ? 13 : 12, lnt = lt - 4;
+  const int lr1 = logN2 % 4 == 0 ? 4 : logN2 % 4, logc = lt - logN2;
+  const long long tile = i >> lt, w = i & ((1ll << lt) - 1), j = w >> 4;
   const long long s = 2 * (((w >> 1) & 7) ^ (j & 7)) + (w & 1);
-  const long long q = s >> lr1, r = s & ((1 << lr1) - 1), beta = j + 256 * q;
+  const long long q = s >> lr1, r = s & ((1 << lr1) - 1), beta = j + (q << lnt);
   const long long b = beta & ((1 << logc) - 1), i2 = (beta >> logc) + (r << (logN2 - lr1));
   return (i2 << 12) + (tile << logc) + b;
 }
@@ -678,11 +680,11 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   // complex64 at 2^13 points: the SMEM-resident line kernel (15 batched instances, 500
   // steps: 4.6 ms against 8.4 ms for the two-sweep kernel)
   const int logn0 = ilog2exact(ntot);
-  // complex64 from 2^20 to 2^23 points: the TMA-fed two-sweep path measured faster than both
-  // (G point-steps/s, 100-step calls: 61.6 against 42.1 at 2^20, 68.6 against 55.1 at 2^22,
-  // 57.2 against 54.0 at 2^23)
+  // complex64 from 2^20 to 2^24 points: the TMA-fed two-sweep path measured faster than both
+  // (G point-steps/s, 100-step calls: 61.6 against 42.1 at 2^20, 79.2 against 55.7 at 2^22,
+  // 73.0 against 54.2 at 2^23, 64.9 against 55.0 at 2^24)
   const bool four_first = prec == LSP_C64 && logn0 >= 20;
-  const bool tma_first = prec == LSP_C64 && logn0 >= 20 && logn0 <= 23;
+  const bool tma_first = prec == LSP_C64 && logn0 >= 20 && logn0 <= 24;
   const bool small_first = prec == LSP_C64 && r == 1 && logn0 == 13;
   const int order_tma[] = {kPathRank1x2, kPathRank1x4, kPathMultipass, kPathSmall};
   const int order_rest[] = {small_first ? kPathSmall : four_first ? kPathRank1x4 : kPathMultipass,

@@ -13,7 +13,7 @@
 
 namespace lsp {
 
-constexpr int kS2MinLog = 16, kS2MaxLog = 23;
+constexpr int kS2MinLog = 16, kS2MaxLog = 24;
 
 bool s2_kernels_16(int v, S2Kernels* k);
 bool s2_kernels_17(int v, S2Kernels* k);
@@ -23,6 +23,7 @@ bool s2_kernels_20(int v, S2Kernels* k);
 bool s2_kernels_21(int v, S2Kernels* k);
 bool s2_kernels_22(int v, S2Kernels* k);
 bool s2_kernels_23(int v, S2Kernels* k);
+bool s2_kernels_24(int v, S2Kernels* k);
 
 bool s2_kernels_for(int m, int v, S2Kernels* k) {
   switch (m) {
@@ -34,6 +35,7 @@ bool s2_kernels_for(int m, int v, S2Kernels* k) {
     case 21: return s2_kernels_21(v, k);
     case 22: return s2_kernels_22(v, k);
     case 23: return s2_kernels_23(v, k);
+    case 24: return s2_kernels_24(v, k);
     default: return false;
   }
 }
@@ -63,7 +65,7 @@ static int encode_cols(CUtensorMap* map, const void* base, int m) {
   const int ln2 = m - kS2LogN1;
   const cuuint64_t dims[2] = {(cuuint64_t)1 << kS2LogN1, (cuuint64_t)1 << ln2};
   const cuuint64_t strides[1] = {((cuuint64_t)1 << kS2LogN1) * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)(kS2Tile >> ln2), (cuuint32_t)std::min(1 << ln2, 256)};
+  const cuuint32_t box[2] = {(cuuint32_t)((1 << s2_logtile(m)) >> ln2), (cuuint32_t)std::min(1 << ln2, 256)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -106,7 +108,7 @@ int s2_upload_desc(lsp_plan p) {
 }
 
 // Grid of one kernel: CTAs resident at once (cached per device and kernel).
-static int s2_grid(const void* fn, size_t smem, int* grid) {
+static int s2_grid(const void* fn, size_t smem, int* grid, int nt = kS2NT) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, int> cache;
   int dev = 0;
@@ -116,7 +118,7 @@ static int s2_grid(const void* fn, size_t smem, int* grid) {
   if (it != cache.end()) { *grid = it->second; return LSP_OK; }
   int per_sm = 0, sms = 0;
   LSP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  LSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kS2NT, smem));
+  LSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
   LSP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (per_sm < 1) return LSP_ERR_UNSUPPORTED;
   *grid = per_sm * sms;
@@ -125,22 +127,22 @@ static int s2_grid(const void* fn, size_t smem, int* grid) {
 }
 
 static int s2_launch(const void* fn, size_t smem, const S2Inst* inst, const int2* map, int ntiles, int* err,
-                     long long spin_limit, cudaStream_t s) {
+                     long long spin_limit, cudaStream_t s, int nt = kS2NT) {
   int grid = 0;
-  int rc = s2_grid(fn, smem, &grid);
+  int rc = s2_grid(fn, smem, &grid, nt);
   if (rc) return rc;
   grid = std::max(1, std::min(ntiles, grid));
   S2Params P{inst, map, ntiles, err, spin_limit};
   void* args[] = {(void*)&P};
-  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kS2NT), args, smem, s));
+  LSP_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, s));
   return LSP_OK;
 }
 
 // Kernel attributes and grids of every kernel of size m, set outside any capture.
 static int s2_prepare(const S2Kernels& K) {
   int grid = 0, rc = LSP_OK;
-  for (int k = 0; k < kS2Kinds && !rc; ++k) rc = s2_grid(K.k[k], K.smem[k], &grid);
-  if (!rc) rc = s2_grid(K.row_kidx, K.smem_row_kidx, &grid);
+  for (int k = 0; k < kS2Kinds && !rc; ++k) rc = s2_grid(K.k[k], K.smem[k], &grid, K.nt);
+  if (!rc) rc = s2_grid(K.row_kidx, K.smem_row_kidx, &grid, K.nt);
   return rc;
 }
 
@@ -149,11 +151,11 @@ static int s2_launch_steps(const S2Kernels& K, bool kidx, const S2Inst* inst, co
                            long long spin_limit, int64_t nsteps, cudaStream_t s) {
   const void* row = kidx ? K.row_kidx : K.k[kS2Row];
   const size_t row_smem = kidx ? K.smem_row_kidx : K.smem[kS2Row];
-  int rc = s2_launch(K.k[kS2Head], K.smem[kS2Head], inst, map, ntiles, err, spin_limit, s);
+  int rc = s2_launch(K.k[kS2Head], K.smem[kS2Head], inst, map, ntiles, err, spin_limit, s, K.nt);
   for (int64_t st = 0; st < nsteps && !rc; ++st) {
-    rc = s2_launch(row, row_smem, inst, map, ntiles, err, spin_limit, s);
-    if (!rc) rc = st + 1 < nsteps ? s2_launch(K.k[kS2Mid], K.smem[kS2Mid], inst, map, ntiles, err, spin_limit, s)
-                                  : s2_launch(K.k[kS2Tail], K.smem[kS2Tail], inst, map, ntiles, err, spin_limit, s);
+    rc = s2_launch(row, row_smem, inst, map, ntiles, err, spin_limit, s, K.nt);
+    if (!rc) rc = st + 1 < nsteps ? s2_launch(K.k[kS2Mid], K.smem[kS2Mid], inst, map, ntiles, err, spin_limit, s, K.nt)
+                                  : s2_launch(K.k[kS2Tail], K.smem[kS2Tail], inst, map, ntiles, err, spin_limit, s, K.nt);
   }
   return rc;
 }
@@ -211,8 +213,8 @@ int s2_spectral(lsp_plan p, cudaStream_t s) {
   if (rc) return rc;
   LSP_CUDA_TRY(cudaMemcpyAsync(p->work, p->u, (size_t)p->ntot * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   const S2Inst* d = (const S2Inst*)p->s2desc + 1;
-  rc = s2_launch(K.k[kS2ColFwd], K.smem[kS2ColFwd], d, nullptr, K.ntiles, p->err, p->spin_limit, s);
-  if (!rc) rc = s2_launch(K.k[kS2RowFwd], K.smem[kS2RowFwd], d, nullptr, K.ntiles, p->err, p->spin_limit, s);
+  rc = s2_launch(K.k[kS2ColFwd], K.smem[kS2ColFwd], d, nullptr, K.ntiles, p->err, p->spin_limit, s, K.nt);
+  if (!rc) rc = s2_launch(K.k[kS2RowFwd], K.smem[kS2RowFwd], d, nullptr, K.ntiles, p->err, p->spin_limit, s, K.nt);
   return rc;
 }
 
@@ -245,16 +247,16 @@ int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, doub
     kind.clear();
     auto rec = [&]() { return cudaEventRecordWithFlags(ev[k++], st, flags) == cudaSuccess ? LSP_OK : LSP_ERR_CUDA; };
     int r = rec();
-    if (!r) r = s2_launch(K.k[kS2Head], K.smem[kS2Head], d, nullptr, K.ntiles, p->err, p->spin_limit, st);
+    if (!r) r = s2_launch(K.k[kS2Head], K.smem[kS2Head], d, nullptr, K.ntiles, p->err, p->spin_limit, st, K.nt);
     kind.push_back(-1);
     if (!r) r = rec();
     for (int64_t step = 0; step < nsteps && !r; ++step) {
-      r = s2_launch(row, row_smem, d, nullptr, K.ntiles, p->err, p->spin_limit, st);
+      r = s2_launch(row, row_smem, d, nullptr, K.ntiles, p->err, p->spin_limit, st, K.nt);
       kind.push_back(2);
       if (!r) r = rec();
       const bool last = step + 1 == nsteps;
       if (!r) r = s2_launch(K.k[last ? kS2Tail : kS2Mid], K.smem[last ? kS2Tail : kS2Mid], d, nullptr, K.ntiles,
-                            p->err, p->spin_limit, st);
+                            p->err, p->spin_limit, st, K.nt);
       kind.push_back(last ? -1 : 0);
       if (!r) r = rec();
     }

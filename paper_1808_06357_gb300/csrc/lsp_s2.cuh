@@ -75,6 +75,22 @@ enum S2Kind { kS2Head = 0, kS2Mid, kS2Tail, kS2ColFwd, kS2Row, kS2RowFwd, kS2Kin
 constexpr int kS2NT = 256, kS2Tile = 4096, kS2LogN1 = 12;
 constexpr unsigned kS2TileBytes = kS2Tile * 8u;
 
+// Tiles of a lattice of 2^M points: 4096 points (one row, or C = 4096 / N2 columns) on 256
+// threads; from 2^24 (N2 >= 4096: a 4096-point column tile would be one column, below the
+// tensor copies' 16-byte rows) 8192 points (two rows, or two columns) on 512 threads, one CTA
+// per SM, each row of a row tile transformed by one 256-thread half.
+constexpr int kS2WideLog = 24;
+template <int M> struct S2Tiles {
+  static constexpr bool WIDE = M >= kS2WideLog;
+  static constexpr int NT = WIDE ? 512 : 256;
+  static constexpr int LOGT = WIDE ? 13 : 12;           // log2 points per tile
+  static constexpr int TILE = 1 << LOGT;
+  static constexpr unsigned BYTES = (unsigned)TILE * 8u;
+  static constexpr int ROWS = TILE >> kS2LogN1;         // rows per row tile
+  static constexpr int MINB = WIDE ? 1 : 2;             // CTAs per SM
+};
+__host__ __device__ __forceinline__ int s2_logtile(int m) { return m >= kS2WideLog ? 13 : 12; }
+
 // Schedules of the kernels (the autotuner's choice per lattice size); all run two
 // CTAs per SM and bring the potential-phase tile of the column sweeps in by TMA:
 //   0: the line twiddles of each radix-16 pass read (through L1) where they are used
@@ -100,7 +116,9 @@ template <int M, int KIND> struct S2Geo {
   static constexpr bool COL = KIND <= kS2ColFwd;
   static constexpr int LN2 = M - kS2LogN1;
   static constexpr int LOGL = COL ? LN2 : kS2LogN1;
-  using G = Line<float2, kS2NT, LOGL, !COL, 1, COL ? col_swizzle(LOGL) : 0>;
+  using T = S2Tiles<M>;
+  static constexpr int NT = T::NT;
+  using G = Line<float2, NT, LOGL, !COL, 1, COL ? col_swizzle(LOGL) : 0>;
   static constexpr int LOGC = G::LOGC;                  // lines per tile
   static constexpr int C = 1 << LOGC;
   static constexpr int BR = COL ? ((1 << LN2) < 256 ? (1 << LN2) : 256) : 0;   // rows per tensor box
@@ -116,13 +134,14 @@ template <int M, int KIND> struct S2Geo {
 template <int M, int KIND, bool KIDX, int V> struct S2Smem {
   using Geo = S2Geo<M, KIND>;
   static constexpr bool TWS = Geo::COL && S2Sched<V>::TWS_COL;
-  static constexpr unsigned KIDX_BYTES = (!Geo::COL && KIDX) ? 4096u : 0u;
-  static constexpr unsigned SLOT = kS2TileBytes + KIDX_BYTES;
+  using T = typename Geo::T;
+  static constexpr unsigned KIDX_BYTES = (!Geo::COL && KIDX) ? (unsigned)T::TILE : 0u;
+  static constexpr unsigned SLOT = T::BYTES + KIDX_BYTES;
   static constexpr unsigned PBUF = 2 * SLOT;
-  static constexpr unsigned TWT = PBUF + (Geo::HAS_P ? kS2TileBytes : 0u);
+  static constexpr unsigned TWT = PBUF + (Geo::HAS_P ? T::BYTES : 0u);
   static constexpr unsigned LUT = TWT + (TWS ? (unsigned)Geo::G::TW_ENTRIES * 8u : 0u);
-  static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // 2 x W_n^{256 r xi2}, r < 16
-  static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 2u * 16u * 8u);
+  static constexpr unsigned TWR = LUT + ((!Geo::COL && KIDX) ? 256u * 8u : 0u);   // 2 x W_n^{256 r xi2}, r < 16, per row
+  static constexpr unsigned USED = TWR + (Geo::COL ? 0u : 2u * (unsigned)T::ROWS * 16u * 8u);
   static constexpr unsigned BYTES = USED + 128u;        // room to align the base to 128 bytes (tensor copies)
 };
 
@@ -140,12 +159,16 @@ template <int M, int KIND, bool KIDX, int V> struct S2Smem {
 //   pass 2 -> 3: element (c, t, e) at 256 c + 16 (c ^ t) + (e ^ c ^ t)
 // Twiddles: pass 2's W_256^{e r} from the row table's [r-1][jm] part; pass 3's
 // W_4096^{(16 t + e) r} stored [r-1][e][t] (the host's row table permutes that part),
-// so that a warp's 32 loads of one r are contiguous.
-struct S2Row {
+// so that a warp's 32 loads of one r are contiguous.  On CTAs of NT = 512 threads each
+// 256-thread half transforms its own row, synchronised by a named barrier of its own.
+template <int NT> struct S2Row {
   static constexpr int kTw3 = 15 * 16;                  // start of pass 3's table
-  static __device__ __forceinline__ int e_of() {
-    return (int)(((threadIdx.x >> 5) << 1) | ((threadIdx.x >> 4) & 1u));
+  static __device__ __forceinline__ int lt() { return (int)(threadIdx.x & 255u); }
+  static __device__ __forceinline__ void sync() {
+    if constexpr (NT == 256) __syncthreads();
+    else asm volatile("bar.sync %0, 256;" ::"r"(1 + (int)(threadIdx.x >> 8)) : "memory");
   }
+  static __device__ __forceinline__ int e_of() { return ((lt() >> 5) << 1) | ((lt() >> 4) & 1); }
   static __device__ __forceinline__ int c_of() { return (int)(threadIdx.x & 15u); }
   // pass-3 butterfly of this thread: the forward's output t is bin xi1 = jn3() + 256 t
   static __device__ __forceinline__ int jn3() { return (c_of() << 4) | e_of(); }
@@ -167,17 +190,17 @@ struct S2Row {
     for (int t = 0; t < 16; ++t) v[t] = o[out_at<16>(t)];
   }
 
-  // v[r] = x[j + 256 r] (j = thread)  ->  v[t] = X[jn3() + 256 t]
+  // v[r] = x[j + 256 r] (j = thread of the half)  ->  v[t] = X[jn3() + 256 t]
   static __device__ __forceinline__ void fwd(float2* sm, const float2* __restrict__ tw, float2 (&v)[16]) {
-    const int j = (int)threadIdx.x, c = c_of(), e = e_of();
+    const int j = lt(), c = c_of(), e = e_of();
     const int a2 = (c << 4) | (e ^ c), b2 = (c << 8) | a2;
     float2 w[15];
     load_tw2(tw, e, w);
     butterfly<-1>(v);
-    __syncthreads();                                    // every thread has read its tile input
+    sync();                                             // every thread has read its tile input
 #pragma unroll
     for (int t = 0; t < 16; ++t) sm[(j << 4) | (t ^ (j & 15))] = v[t];
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = sm[(r << 8) + a2];
 #pragma unroll
@@ -197,7 +220,7 @@ struct S2Row {
 
   // v[t] = X[jn3() + 256 t]  ->  v[r] = unnormalised inverse DFT at x[j + 256 r]
   static __device__ __forceinline__ void inv(float2* sm, const float2* __restrict__ tw, float2 (&v)[16]) {
-    const int j = (int)threadIdx.x, c = c_of(), e = e_of();
+    const int j = lt(), c = c_of(), e = e_of();
     const int a2 = (c << 4) | (e ^ c), b2 = (c << 8) | a2;
     float2 w[15];
     load_tw3(tw, e, c, w);
@@ -217,7 +240,7 @@ struct S2Row {
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm[(r << 8) + a2] = v[r];
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int t = 0; t < 16; ++t) v[t] = sm[(j << 4) | (t ^ (j & 15))];
     butterfly<+1>(v);
@@ -259,15 +282,15 @@ __device__ __forceinline__ void s2_wait(unsigned long long* b, unsigned parity, 
 // order (a fence here stalls the issuing warp on its own outstanding global stores, and
 // every other warp with it at the tile's next barrier).
 //
-// Column tile t of an n = 2^m array (tensor map `map`): C = 2^(24 - m) columns, boxes of
+// Column tile t of an n = 2^m array (tensor map `map`): C = tile / N2 columns, boxes of
 // min(N2, 256) rows, into dst (thread 0 only).
 __device__ __forceinline__ void s2_issue_cols(const CUtensorMap* map, int m, int t, unsigned char* dst,
                                               unsigned long long* b) {
-  const int ln2 = m - kS2LogN1;
-  const int c = 1 << (kS2LogN1 - ln2);
+  const int ln2 = m - kS2LogN1, lt = s2_logtile(m);
+  const int c = 1 << (lt - ln2);
   const int br = (1 << ln2) < 256 ? (1 << ln2) : 256;
   const int nb = (1 << ln2) / br;
-  mbar_arrive_expect_tx(b, kS2TileBytes);
+  mbar_arrive_expect_tx(b, 8u << lt);
   for (int k = 0; k < nb; ++k) tma_load_2d(dst + (size_t)k * br * c * 8, map, t * c, k * br, b);
 }
 
@@ -275,8 +298,8 @@ __device__ __forceinline__ void s2_issue_cols(const CUtensorMap* map, int m, int
 // global memory: tensor stores in thread 0's bulk group, after every thread's writes of src,
 // their proxy fence and a CTA barrier.
 __device__ __forceinline__ void s2_store_cols(const CUtensorMap* map, int m, int t, const unsigned char* src) {
-  const int ln2 = m - kS2LogN1;
-  const int c = 1 << (kS2LogN1 - ln2);
+  const int ln2 = m - kS2LogN1, lt = s2_logtile(m);
+  const int c = 1 << (lt - ln2);
   const int br = (1 << ln2) < 256 ? (1 << ln2) : 256;
   const int nb = (1 << ln2) / br;
   for (int k = 0; k < nb; ++k) tma_store_2d(map, t * c, k * br, src + (size_t)k * br * c * 8);
@@ -284,25 +307,28 @@ __device__ __forceinline__ void s2_store_cols(const CUtensorMap* map, int m, int
 }
 
 // Issue the copies of local tile t of instance I into slot `dst` (thread 0 only): a column
-// tile, or a row with its K byte index when the instance has one and the slot has room
-// for it (KIDX).
+// tile, or a row tile (one or two rows) with its K byte index when the instance has one and
+// the slot has room for it (KIDX).
 template <bool COL, bool KIDX>
 __device__ __forceinline__ void s2_issue_tile(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
   if constexpr (COL) {
     s2_issue_cols(&I.tu, I.m, t, dst, b);
   } else {
+    const int lt = s2_logtile(I.m);
     const bool kx = KIDX && I.kidx != nullptr;
-    mbar_arrive_expect_tx(b, kS2TileBytes + (kx ? 4096u : 0u));
-    bulk_g2s(dst, I.u + ((size_t)t << kS2LogN1), kS2TileBytes, b);
-    if (kx) bulk_g2s(dst + kS2TileBytes, I.kidx + ((size_t)t << kS2LogN1), 4096u, b);
+    mbar_arrive_expect_tx(b, (8u << lt) + (kx ? 1u << lt : 0u));
+    bulk_g2s(dst, I.u + ((size_t)t << lt), 8u << lt, b);
+    if (kx) bulk_g2s(dst + (8u << lt), I.kidx + ((size_t)t << lt), 1u << lt, b);
   }
 }
 
-// The potential-phase tile of column tile t: 32 KiB, contiguous in the tables' tile order.
+// The potential-phase tile of column tile t: the tile's phases, contiguous in the tables'
+// tile order (32 or 64 KiB).
 template <int KIND>
 __device__ __forceinline__ void s2_issue_p(const S2Inst& I, int t, unsigned char* dst, unsigned long long* b) {
-  mbar_arrive_expect_tx(b, kS2TileBytes);
-  bulk_g2s(dst, (KIND == kS2Mid ? I.Pf : I.Ph) + ((size_t)t << kS2LogN1), kS2TileBytes, b);
+  const int lt = s2_logtile(I.m);
+  mbar_arrive_expect_tx(b, 8u << lt);
+  bulk_g2s(dst, (KIND == kS2Mid ? I.Pf : I.Ph) + ((size_t)t << lt), 8u << lt, b);
 }
 
 // W_n^a (a < n) from the two-level table: W_N1^{a >> LN2} W_n^{a mod N2}.
@@ -386,49 +412,59 @@ __device__ __forceinline__ void s2_col_tile(const S2Inst& I, int t, float2* slot
   }
 }
 
-// One row tile (row t = xi2, 4096 contiguous points); the K byte index of the row sits
-// after the state in the slot, thread-major (thread jn's 16 bytes, for its forward outputs
-// q = 0..15, together).
-// W_n^{256 r t}, r < 16, of row t into twr (threads 0..15).
+// One row tile: ROWS rows xi2 = t ROWS + g of 4096 contiguous points, row g transformed by
+// threads 256 g .. 256 g + 255; the K byte index of the rows sits after the state in the slot,
+// thread-major within each row (thread jn's 16 bytes, for its forward outputs q = 0..15,
+// together).
+// W_n^{256 r xi2}, r < 16, of the tile's rows into twr (16 per row; threads 0 .. 16 ROWS - 1).
 template <int M>
 __device__ __forceinline__ void s2_row_twr(const S2Inst& I, int t, float2* twr) {
-  if (threadIdx.x < 16)
-    twr[threadIdx.x] = s2_wn<M>(I, ((unsigned)t * (threadIdx.x << (kS2LogN1 - 4))) & ((1u << M) - 1u));
+  constexpr int ROWS = S2Tiles<M>::ROWS;
+  if (threadIdx.x < 16u * ROWS) {
+    const unsigned row = (unsigned)(t * ROWS) + (threadIdx.x >> 4), r = threadIdx.x & 15u;
+    twr[threadIdx.x] = s2_wn<M>(I, (row * (r << (kS2LogN1 - 4))) & ((1u << M) - 1u));
+  }
 }
 
 template <int M, int KIND, bool KIDX, int V>
 __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot, const float2* tw, const float2* lut,
                                             const float2* twr) {
+  using T = S2Tiles<M>;
+  using R = S2Row<T::NT>;
   constexpr int LOGL = kS2LogN1;
   constexpr unsigned NMASK = (1u << M) - 1u;
   float2 v[16];
-  const int jn = (int)threadIdx.x, j3 = S2Row::jn3();
-  // pass-1 pattern: register r holds k1 = jn + 256 r of row t
+  const int g = T::ROWS == 1 ? 0 : (int)(threadIdx.x >> 8);
+  const int rt = t * T::ROWS + g;                       // this half's row xi2
+  float2* sl = slot + (g << LOGL);
+  twr += 16 * g;
+  const int jn = R::lt(), j3 = R::jn3();
+  // pass-1 pattern: register r holds k1 = jn + 256 r of row rt
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = slot[jn + (r << (LOGL - 4))];
+  for (int r = 0; r < 16; ++r) v[r] = sl[jn + (r << (LOGL - 4))];
   uint4 kb = make_uint4(0, 0, 0, 0);
   float2 kv[(KIND == kS2Row && !KIDX) ? 16 : 1];
   if constexpr (KIND == kS2Row) {
     if constexpr (KIDX) {
-      kb = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(slot) + kS2TileBytes)[jn];
+      kb = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(slot) + T::BYTES + (g << LOGL))[jn];
     } else {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + ((size_t)t << LOGL) + jn + (q << (LOGL - 4)));
+      for (int q = 0; q < 16; ++q) kv[q] = ldtab(I.K + ((size_t)rt << LOGL) + jn + (q << (LOGL - 4)));
     }
   }
   // the slot becomes the exchange buffer: the transform's first barrier precedes its first write
-  // four-step twiddle W_n^{k1 t} = W_n^{j t} W_n^{256 r t} (twr written before the tile's barrier)
-  const float2 wb = s2_wn<M>(I, ((unsigned)t * (unsigned)jn) & NMASK);
+  // four-step twiddle W_n^{k1 rt} = W_n^{j rt} W_n^{256 r rt} (twr written before the tile's barrier)
+  const float2 wb = s2_wn<M>(I, ((unsigned)rt * (unsigned)jn) & NMASK);
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = twmul(twmul(v[r], twr[r]), wb);
-  S2Row::fwd(slot, tw, v);                              // v[q] = bin xi1 = j3 + 256 q of row t
+  R::fwd(sl, tw, v);                                    // v[q] = bin xi1 = j3 + 256 q of row rt
   if constexpr (KIND == kS2RowFwd) {
     const int N2 = 1 << (M - kS2LogN1);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int xi1 = j3 + (q << (LOGL - 4));
       const float2 x = cscale(v[q], I.inv_n);
-      I.spec[t + (size_t)xi1 * N2] = make_double2((double)x.x, (double)x.y);
+      I.spec[rt + (size_t)xi1 * N2] = make_double2((double)x.x, (double)x.y);
     }
   } else {
     if constexpr (KIDX) {
@@ -439,14 +475,14 @@ __device__ __forceinline__ void s2_row_tile(const S2Inst& I, int t, float2* slot
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = apply_phase(v[q], kv[q]);
     }
-    S2Row::inv(slot, tw, v);
+    R::inv(sl, tw, v);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)t << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
+    for (int r = 0; r < 16; ++r) stst(I.u + ((size_t)rt << LOGL) + jn + (r << (LOGL - 4)), twmulc(twmulc(v[r], wb), twr[r]));
   }
 }
 
 template <int M, int KIND, bool KIDX, int V>
-__global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_constant__ S2Params P) {
+__global__ void __launch_bounds__(S2Tiles<M>::NT, S2Tiles<M>::MINB) s2_sweep(const __grid_constant__ S2Params P) {
   using Geo = S2Geo<M, KIND>;
   using SM = S2Smem<M, KIND, KIDX, V>;
   extern __shared__ __align__(128) unsigned char smdyn[];
@@ -467,7 +503,7 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
   const float2* tw = Geo::COL ? P.inst[0].tw_cols : P.inst[0].tw_rows;
   if constexpr (SM::TWS) {
     float2* tws = reinterpret_cast<float2*>(smraw + SM::TWT);
-    for (int k = threadIdx.x; k < Geo::G::TW_ENTRIES; k += kS2NT) tws[k] = __ldg(tw + k);
+    for (int k = threadIdx.x; k < Geo::G::TW_ENTRIES; k += Geo::NT) tws[k] = __ldg(tw + k);
     tw = tws;
   }
   auto inst_of = [&](int tt, int& local) -> const S2Inst& {
@@ -478,10 +514,11 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
   if constexpr (!Geo::COL && KIDX) {
     // one instance: its K table once; a batch reloads the table of each tile's instance below
     if (!P.map)
-      for (int k = threadIdx.x; k < P.inst[0].nlut; k += kS2NT) lut[k] = P.inst[0].klut[k];
+      for (int k = threadIdx.x; k < P.inst[0].nlut; k += Geo::NT) lut[k] = P.inst[0].klut[k];
   }
   __syncthreads();
   float2* twr = reinterpret_cast<float2*>(smraw + SM::TWR);   // row sweeps: per-tile twiddles, by tile parity
+  constexpr int TWR_SET = 16 * Geo::T::ROWS;
   int t = (int)blockIdx.x;
   if (t >= P.ntiles) return;
   {
@@ -499,7 +536,7 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
     if constexpr (!Geo::COL && KIDX) {
       if (P.map) {                                       // batch: this instance's K table
         __syncthreads();
-        for (int k = threadIdx.x; k < I.nlut; k += kS2NT) lut[k] = I.klut[k];
+        for (int k = threadIdx.x; k < I.nlut; k += Geo::NT) lut[k] = I.klut[k];
       }
     }
     __syncthreads();                                    // tile i - 1 done; the wait above ended in every thread
@@ -509,7 +546,7 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
       const S2Inst& In = inst_of(t + G, ln);
       if (threadIdx.x == 0) s2_issue_tile<Geo::COL, KIDX>(In, ln, smraw + (size_t)(s ^ 1) * SM::SLOT, &mb[s ^ 1]);
       // the next row's twiddles: the buffer of parity i + 1 was last read in tile i - 1
-      if constexpr (!Geo::COL) s2_row_twr<M>(In, ln, twr + 16 * (s ^ 1));
+      if constexpr (!Geo::COL) s2_row_twr<M>(In, ln, twr + TWR_SET * (s ^ 1));
     }
     if constexpr (Geo::HAS_P) {
       if (threadIdx.x == 0) {
@@ -521,7 +558,7 @@ __global__ void __launch_bounds__(kS2NT, kS2MinBlocks) s2_sweep(const __grid_con
       s2_col_tile<M, KIND, V>(I, l, reinterpret_cast<float2*>(slot), tw,
                               reinterpret_cast<float2*>(smraw + SM::PBUF), &mb[2], (unsigned)i & 1u, P, &fail);
     else
-      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), tw, lut, twr + 16 * s);
+      s2_row_tile<M, KIND, KIDX, V>(I, l, reinterpret_cast<float2*>(slot), tw, lut, twr + TWR_SET * s);
   }
   if constexpr (Geo::HAS_P && s2_tma_store<M>()) {
     if (threadIdx.x == 0) bulk_wait_all();              // the last tile's stores, before the CTA ends
@@ -535,6 +572,7 @@ struct S2Kernels {
   size_t smem[kS2Kinds] = {};
   size_t smem_row_kidx = 0;
   int ntiles = 0;                                       // tiles per sweep (both geometries)
+  int nt = kS2NT;                                       // threads per CTA
 };
 
 template <int M, int V> S2Kernels s2_kernels_v() {
@@ -553,7 +591,8 @@ template <int M, int V> S2Kernels s2_kernels_v() {
   K.smem[kS2Row] = S2Smem<M, kS2Row, false, V>::BYTES;
   K.smem[kS2RowFwd] = S2Smem<M, kS2RowFwd, false, V>::BYTES;
   K.smem_row_kidx = S2Smem<M, kS2Row, true, V>::BYTES;
-  K.ntiles = 1 << (M - kS2LogN1);
+  K.ntiles = 1 << (M - S2Tiles<M>::LOGT);
+  K.nt = S2Tiles<M>::NT;
   return K;
 }
 

@@ -1,7 +1,9 @@
 """The TMA-fed two-sweep rank-1 path (execution path 4) against the FP64 oracle (GB300).
 
 Rows of 4096 points and columns of n / 4096 points: n = 2^20 .. 2^23 covers column
-tiles of 16, 8, 4 and 2 columns (tensor boxes of 128, 64, 32 and 16 bytes per row).
+tiles of 16, 8, 4 and 2 columns (tensor boxes of 128, 64, 32 and 16 bytes per row); n = 2^24
+runs tiles of 8192 points on 512-thread CTAs (two rows, each transformed by one half of the
+CTA, or two 4096-point columns).
 """
 
 import numpy as np
@@ -33,7 +35,8 @@ def _plan(lib, inst, prec="c64"):
     return plan, v, u0
 
 
-@pytest.mark.parametrize("m,nsteps", [(16, 20), (17, 5), (18, 17), (19, 4), (20, 20), (21, 7), (22, 17), (23, 3)])
+@pytest.mark.parametrize("m,nsteps", [(16, 20), (17, 5), (18, 17), (19, 4), (20, 20), (21, 7), (22, 17), (23, 3),
+                                      (24, 2)])
 def test_tma_two_sweep_matches_oracle(lib, m, nsteps):
     """Every sweep kind of the path (head, row with the byte-index K, mid, tail), plain launches
     below 16 steps and the replayed graph from 16 on, against the oracle's steps."""
@@ -50,6 +53,28 @@ def test_tma_two_sweep_matches_oracle(lib, m, nsteps):
     # spectral output (column forward sweep, row forward sweep with 1/n) against the oracle
     spec = plan.get_state(space="spectral", prec="c128").cpu().numpy()
     assert _rel(spec, S.coeffs(ref, inst.n)) < TOL64
+    plan.destroy()
+
+
+def test_wide_tiles_every_schedule_graph_replay(lib):
+    """n = 2^24 (8192-point tiles, 512 threads): 16 steps replayed from the captured graph under
+    each schedule, against one oracle run; spectral output under the default schedule."""
+    inst = w.c2(24)
+    plan, v, u0 = _plan(lib, inst)
+    norms, _ = L.minl2_norms_dp(inst.Z, inst.n)
+    ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 16)
+    import torch
+    for sched in (0, 1, 2):
+        plan.set_schedule(sched)
+        plan.set_state(torch.from_numpy(u0).cuda())
+        plan.strang_steps(inst.dt, 16)
+        assert plan.status() == 0
+        err = _rel(plan.get_state(prec="c128").cpu().numpy(), ref)
+        assert err < TOL64, (sched, err)
+    plan.set_schedule(1)
+    plan.set_state(torch.from_numpy(u0).cuda())
+    plan.strang_steps(inst.dt, 16)
+    assert _rel(plan.get_state(space="spectral", prec="c128").cpu().numpy(), S.coeffs(ref, inst.n)) < TOL64
     plan.destroy()
 
 
