@@ -71,8 +71,9 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * lsp_plan_create -- build a plan for one TDSE instance on one device.
  *   out        receives the plan handle.
  *   d          spatial dimension, 1 <= d <= 64.
- *   r          lattice rank, 1 <= r <= 2 (r = 1: rank-1 lattice Lambda(z, n), Sec. 2.1;
- *              r = 2: rank-2 lattice Lambda(Z, n) in canonical form, Def. 1).
+ *   r          lattice rank, 1 <= r <= 4 (r = 1: rank-1 lattice Lambda(z, n), Sec. 2.1;
+ *              r >= 2: rank-r lattice Lambda(Z, n) in canonical form, Def. 1, with the
+ *              r-D transform of Sec. 2.5; ranks 3 and 4 run on the SMEM-resident path).
  *   n          r moduli n_1..n_r (host); n = prod n_i points.
  *   Z          d*r generating-vector entries (host), row-major: Z[j*r + i] is
  *              component j of z_i.
@@ -83,16 +84,18 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *   prec       LSP_C64 or LSP_C128.
  *   gamma      gamma = hbar / sqrt(mass) > 0 (Sec. 1).
  *   device     CUDA device ordinal.
- * Errors: BAD_ARG, NOT_CANONICAL, NOT_INJECTIVE, TOO_LARGE, OOM, CUDA,
- * UNSUPPORTED.  On error *out is set to NULL and nothing is leaked.
+ * Errors: BAD_ARG, NOT_CANONICAL (n_{i+1} not dividing n_i, or fewer than n distinct
+ * points), NOT_INJECTIVE, TOO_LARGE, OOM, CUDA, UNSUPPORTED; the argument, rank and
+ * divisibility checks come before any device call.  On error *out is set to NULL and
+ * nothing is leaked.
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
  * 0, 3, 1, 4, but for complex64 1, 3, 0, 4 at n = 2^13, 4, 3, 0, 1 from 2^20 to
  * 2^24 and 3, 0, 1, 4 above;
- * rank 2: 1, 2; reported by lsp_plan_info, changed by lsp_plan_set_path or
+ * rank 2: 1, 2; ranks 3 and 4: 1; reported by lsp_plan_info, changed by lsp_plan_set_path or
  * lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
- *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, rank 1 or 2
+ *   1 SMEM-resident: any n with 2 n sizeof(complex) <= 200 KiB, any rank
  *     (rank 1 with n = 2^11 .. 2^13 (complex64) or 2^11 .. 2^12 (complex128): the
  *     state stays in registers across the steps, one line FFT per step);
  *   2 four-sweep, rank 2: (n_1, n_2) = (2^m1, 2^m2) with (m1, m2) one of

@@ -151,7 +151,7 @@ def _buf(x, output: bool = False):
 
 
 class Plan:
-    """One TDSE instance on a rank-1 or rank-2 lattice (lsp_plan_create)."""
+    """One TDSE instance on a rank-r lattice, r <= 4 (lsp_plan_create)."""
 
     def __init__(self, Z, n, gamma: float, prec="c64", aa: str = "minl2", index_set=None,
                  device: int = 0):

@@ -31,19 +31,39 @@ __global__ void dp_init(int32_t* f, long long n) {
     f[i] = i == 0 ? 0 : kInf;
 }
 
-__global__ void dp_step(const int32_t* __restrict__ f, int32_t* __restrict__ g, long long n1, long long n2,
-                        long long s1, long long s2, int B) {
-  const long long n = n1 * n2;
+// The residue group Z_{n_1} x ... x Z_{n_R} of a rank-R lattice, bins in lexicographic (chi)
+// order; also used for one DP component's shift s_i = z_{j,i} mod n_i.
+struct ResGroup {
+  long long n[kMaxRank];
+};
+
+template <int R> __device__ __forceinline__ long long res_index(const long long (&a)[R], const ResGroup& G) {
+  long long idx = a[0];
+#pragma unroll
+  for (int i = 1; i < R; ++i) idx = idx * G.n[i] + a[i];
+  return idx;
+}
+
+// One DP component: g(xi) = min_{|t| <= B} f(xi - t s) + t^2 over the residue group.
+template <int R>
+__global__ void dp_step(const int32_t* __restrict__ f, int32_t* __restrict__ g, ResGroup G, ResGroup S, int B) {
+  long long n = 1;
+#pragma unroll
+  for (int i = 0; i < R; ++i) n *= G.n[i];
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    long long x1 = c / n2, x2 = c - x1 * n2;
-    long long a1 = (x1 + (B * s1) % n1) % n1;     // xi - t z_j at t = -B
-    long long a2 = (x2 + (B * s2) % n2) % n2;
+    long long a[R], rem = c;
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) {
+      const long long x = rem % G.n[i];
+      rem /= G.n[i];
+      a[i] = (x + (B * S.n[i]) % G.n[i]) % G.n[i];   // xi - t s at t = -B
+    }
     int best = kInf;
     for (int t = -B; t <= B; ++t) {
-      int val = __ldg(f + a1 * n2 + a2);
+      const int val = __ldg(f + res_index<R>(a, G));
       if (val < kInf) best = min(best, val + t * t);
-      a1 -= s1; if (a1 < 0) a1 += n1;
-      a2 -= s2; if (a2 < 0) a2 += n2;
+#pragma unroll
+      for (int i = 0; i < R; ++i) { a[i] -= S.n[i]; if (a[i] < 0) a[i] += G.n[i]; }
     }
     g[c] = best;
   }
@@ -59,24 +79,35 @@ __global__ void dp_max(const int32_t* f, long long n, int* out) {
 
 // Recover one minimal vector per bin from the stored DP levels: walk the
 // components backwards taking the first t (in -B..B order) that attains the level.
-__global__ void dp_backtrack(const int32_t* __restrict__ levels, long long n1, long long n2,
-                             const long long* __restrict__ s1, const long long* __restrict__ s2, int d, int B,
-                             int32_t* __restrict__ h) {
-  const long long n = n1 * n2;
+// s[i d + j] = z_{j,i} mod n_i.
+template <int R>
+__global__ void dp_backtrack(const int32_t* __restrict__ levels, ResGroup G, const long long* __restrict__ s, int d,
+                             int B, int32_t* __restrict__ h) {
+  long long n = 1;
+#pragma unroll
+  for (int i = 0; i < R; ++i) n *= G.n[i];
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    long long x1 = c / n2, x2 = c - x1 * n2;
+    long long x[R], rem = c;
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) { x[i] = rem % G.n[i]; rem /= G.n[i]; }
     for (int j = d; j >= 1; --j) {
       const int32_t* fj = levels + (size_t)j * n;
       const int32_t* fp = levels + (size_t)(j - 1) * n;
-      int cur = fj[x1 * n2 + x2];
-      long long a1 = (x1 + (B * s1[j - 1]) % n1) % n1;
-      long long a2 = (x2 + (B * s2[j - 1]) % n2) % n2;
+      const int cur = fj[res_index<R>(x, G)];
+      long long a[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) a[i] = (x[i] + (B * s[i * d + j - 1]) % G.n[i]) % G.n[i];
       int pick = 0;
       for (int t = -B; t <= B; ++t) {
-        int val = fp[a1 * n2 + a2];
-        if (val < kInf && val + t * t == cur) { pick = t; x1 = a1; x2 = a2; break; }
-        a1 -= s1[j - 1]; if (a1 < 0) a1 += n1;
-        a2 -= s2[j - 1]; if (a2 < 0) a2 += n2;
+        const int val = fp[res_index<R>(a, G)];
+        if (val < kInf && val + t * t == cur) {
+          pick = t;
+#pragma unroll
+          for (int i = 0; i < R; ++i) x[i] = a[i];
+          break;
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) { a[i] -= s[i * d + j - 1]; if (a[i] < 0) a[i] += G.n[i]; }
       }
       h[c * d + (j - 1)] = pick;
     }
@@ -87,9 +118,26 @@ static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 2
 
 // Runs the DP; on success `out` (n int32) holds the norms and *box the half-width used.
 // When `levels` is non-null it receives all d+1 levels (for backtracking) with box fixed.
+static ResGroup res_group(lsp_plan p) {
+  ResGroup G{};
+  for (int i = 0; i < kMaxRank; ++i) G.n[i] = p->n[i];
+  return G;
+}
+
+static void launch_dp_step(int r, const int32_t* f, int32_t* g, long long n, const ResGroup& G, const ResGroup& S,
+                           int B) {
+  switch (r) {
+    case 1: dp_step<1><<<grid_for(n), 256>>>(f, g, G, S, B); break;
+    case 2: dp_step<2><<<grid_for(n), 256>>>(f, g, G, S, B); break;
+    case 3: dp_step<3><<<grid_for(n), 256>>>(f, g, G, S, B); break;
+    default: dp_step<4><<<grid_for(n), 256>>>(f, g, G, S, B); break;
+  }
+}
+
 static int minl2_dp(lsp_plan p, int32_t* out, int* box, int32_t* levels, int fixed_box) {
-  const long long n1 = p->n[0], n2 = p->r == 2 ? p->n[1] : 1;
-  const long long n = n1 * n2;
+  const long long n1 = p->n[0];
+  const long long n = p->ntot;
+  const ResGroup G = res_group(p);
   const int d = p->d;
   int B;
   if (fixed_box > 0) {
@@ -112,11 +160,11 @@ static int minl2_dp(lsp_plan p, int32_t* out, int* box, int32_t* levels, int fix
     int32_t* a = levels ? levels : f;
     dp_init<<<grid_for(n), 256>>>(a, n);
     for (int j = 0; j < d; ++j) {
-      long long s1 = ((p->Z[j * p->r + 0] % n1) + n1) % n1;
-      long long s2 = p->r == 2 ? ((p->Z[j * p->r + 1] % n2) + n2) % n2 : 0;
+      ResGroup S{};
+      for (int i = 0; i < p->r; ++i) S.n[i] = ((p->Z[j * p->r + i] % p->n[i]) + p->n[i]) % p->n[i];
       int32_t* src = levels ? levels + (size_t)j * n : (j % 2 == 0 ? f : g);
       int32_t* dst = levels ? levels + (size_t)(j + 1) * n : (j % 2 == 0 ? g : f);
-      dp_step<<<grid_for(n), 256>>>(src, dst, n1, n2, s1, s2, B);
+      launch_dp_step(p->r, src, dst, n, G, S, B);
     }
     int32_t* res = levels ? levels + (size_t)d * n : (d % 2 == 1 ? g : f);
     if (cudaMemset(dmax, 0, sizeof(int)) != cudaSuccess) { rc = LSP_ERR_CUDA; break; }
@@ -569,7 +617,7 @@ static int setup_path_tables(lsp_plan p, int path) {
     if ((rc = upload(p, &p->tw_pass, tw))) return rc;
   }
   p->N1 = (int)p->n[p->r - 1];
-  p->N2 = p->r == 2 ? (int)p->n[0] : 1;
+  p->N2 = (int)(p->ntot / p->N1);
   return small_upload_desc(p, 0);
 }
 
@@ -648,7 +696,7 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
                     const int32_t* index_set, int64_t m, int aa_mode, int prec, double gamma, int device) {
   if (!out) return LSP_ERR_BAD_ARG;
   *out = nullptr;
-  if (d < 1 || d > 64 || r < 1 || r > 2 || !n || !Z) return LSP_ERR_BAD_ARG;
+  if (d < 1 || d > 64 || r < 1 || r > kMaxRank || !n || !Z) return LSP_ERR_BAD_ARG;
   if (prec != LSP_C64 && prec != LSP_C128) return LSP_ERR_BAD_ARG;
   if (aa_mode != LSP_AA_MINL2 && aa_mode != LSP_AA_EXPLICIT) return LSP_ERR_BAD_ARG;
   if (!(gamma > 0.0) || !isfinite(gamma)) return LSP_ERR_BAD_ARG;
@@ -659,14 +707,16 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
     ntot *= n[i];
     if (ntot > (1ll << 30)) return LSP_ERR_TOO_LARGE;
   }
-  if (r == 2 && n[0] % n[1] != 0) return LSP_ERR_NOT_CANONICAL;       // n_2 | n_1 (Def. 1)
+  for (int i = 0; i + 1 < r; ++i)
+    if (n[i] % n[i + 1] != 0) return LSP_ERR_NOT_CANONICAL;          // n_{i+1} | n_i (Def. 1)
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) { cudaGetLastError(); return LSP_ERR_CUDA; }
 
   lsp_plan p = new (std::nothrow) lsp_plan_s();
   if (!p) return LSP_ERR_OOM;
   p->device = device; p->d = d; p->r = r; p->prec = prec; p->gamma = gamma; p->aa_mode = aa_mode;
-  p->n[0] = n[0]; p->n[1] = r == 2 ? n[1] : 1; p->ntot = ntot;
+  for (int i = 0; i < kMaxRank; ++i) p->n[i] = i < r ? n[i] : 1;
+  p->ntot = ntot;
   p->Z.assign(Z, Z + (size_t)d * r);
   for (int j = 0; j < d; ++j)
     for (int i = 0; i < r; ++i) { long long ni = p->n[i]; p->Z[j * r + i] = ((p->Z[j * r + i] % ni) + ni) % ni; }
@@ -948,13 +998,14 @@ int lsp_get_state(lsp_plan p, void* out, int out_prec, int space, int on_device,
 
 int lsp_lattice_points(lsp_plan p, double* x) {
   if (!p || !x) return LSP_ERR_BAD_ARG;
-  const long long N = p->ntot, n1 = p->n[0], n2 = p->n[1];
+  const long long N = p->ntot;
   for (long long k = 0; k < N; ++k) {
-    long long k1 = p->r == 2 ? k / n2 : k, k2 = p->r == 2 ? k % n2 : 0;
+    long long kap[kMaxRank] = {0, 0, 0, 0}, rem = k;       // kappa, lexicographic (Sec. 2.5)
+    for (int i = p->r - 1; i >= 0; --i) { kap[i] = rem % p->n[i]; rem /= p->n[i]; }
     for (int j = 0; j < p->d; ++j) {
-      // N p = z_1 k1 (N/n1) + z_2 k2 (N/n2) mod N  (Def. 1)
-      long long q = mulmod(mulmod(p->Z[j * p->r], k1, N), N / n1, N);
-      if (p->r == 2) q = (q + mulmod(mulmod(p->Z[j * p->r + 1], k2, N), N / n2, N)) % N;
+      // N p = sum_i z_i kappa_i (N / n_i) mod N  (Def. 1)
+      long long q = 0;
+      for (int i = 0; i < p->r; ++i) q = (q + mulmod(mulmod(p->Z[j * p->r + i], kap[i], N), N / p->n[i], N)) % N;
       x[k * p->d + j] = (double)q / (double)N;
     }
   }
@@ -974,24 +1025,29 @@ int lsp_index_table(lsp_plan p, int32_t* h) {
   if (!p || !h) return LSP_ERR_BAD_ARG;
   if (p->aa_mode == LSP_AA_EXPLICIT) return LSP_ERR_UNSUPPORTED;
   DeviceGuard g(p->device);
-  const long long n = p->ntot, n1 = p->n[0], n2 = p->n[1];
-  const int d = p->d;
+  const long long n = p->ntot;
+  const int d = p->d, r = p->r;
   int32_t* levels = nullptr;
   int32_t* dh = nullptr;
   long long* ds = nullptr;
   int rc = LSP_OK;
   if (cudaMalloc(&levels, (size_t)(d + 1) * n * sizeof(int32_t)) != cudaSuccess) return LSP_ERR_OOM;
   if (cudaMalloc(&dh, (size_t)n * d * sizeof(int32_t)) != cudaSuccess) { cudaFree(levels); return LSP_ERR_OOM; }
-  if (cudaMalloc(&ds, 2 * (size_t)d * sizeof(long long)) != cudaSuccess) { cudaFree(levels); cudaFree(dh); return LSP_ERR_OOM; }
-  std::vector<long long> s((size_t)2 * d);
-  for (int j = 0; j < d; ++j) {
-    s[j] = p->Z[j * p->r];
-    s[d + j] = p->r == 2 ? p->Z[j * p->r + 1] : 0;
-  }
+  if (cudaMalloc(&ds, (size_t)r * d * sizeof(long long)) != cudaSuccess) { cudaFree(levels); cudaFree(dh); return LSP_ERR_OOM; }
+  std::vector<long long> s((size_t)r * d);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < d; ++j) s[(size_t)i * d + j] = p->Z[j * r + i];
   cudaMemcpy(ds, s.data(), s.size() * sizeof(long long), cudaMemcpyHostToDevice);
   rc = minl2_dp(p, nullptr, nullptr, levels, p->dp_box);
   if (!rc) {
-    dp_backtrack<<<grid_for(n), 256>>>(levels, n1, n2, ds, ds + d, d, p->dp_box, dh);
+    const ResGroup G = res_group(p);
+    const int B = p->dp_box;
+    switch (r) {
+      case 1: dp_backtrack<1><<<grid_for(n), 256>>>(levels, G, ds, d, B, dh); break;
+      case 2: dp_backtrack<2><<<grid_for(n), 256>>>(levels, G, ds, d, B, dh); break;
+      case 3: dp_backtrack<3><<<grid_for(n), 256>>>(levels, G, ds, d, B, dh); break;
+      default: dp_backtrack<4><<<grid_for(n), 256>>>(levels, G, ds, d, B, dh); break;
+    }
     if (cudaMemcpy(h, dh, (size_t)n * d * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) rc = LSP_ERR_CUDA;
   }
   cudaFree(levels); cudaFree(dh); cudaFree(ds);
@@ -1071,8 +1127,8 @@ static std::string tune_key(lsp_plan p, int64_t nsteps) {
   for (int c = 0; c < kNumPaths; ++c)
     if (path_available(p, c)) mask |= 1 << c;
   char buf[256];
-  snprintf(buf, sizeof(buf), "|%d|%d|%lld|%lld|%d|%lld", p->prec, p->r, (long long)p->n[0], (long long)p->n[1], mask,
-           (long long)nsteps);
+  snprintf(buf, sizeof(buf), "|%d|%d|%lld|%lld|%lld|%lld|%d|%lld", p->prec, p->r, (long long)p->n[0],
+           (long long)p->n[1], (long long)p->n[2], (long long)p->n[3], mask, (long long)nsteps);
   return dev + buf;
 }
 

@@ -41,6 +41,10 @@ enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2, kPathRank1x4
 // --------------------------------------------------------------------------
 // Plan
 // --------------------------------------------------------------------------
+// Largest lattice rank (Sec. 2.5: rank-r lattices, an r-D transform): every rank runs on the
+// SMEM-resident path; ranks 1 and 2 also on the multipass paths.
+constexpr int kMaxRank = 4;
+
 struct SmallAxis {
   int len;          // axis length n_i
   int stride;       // element stride of the axis in kappa / chi order
@@ -81,7 +85,7 @@ inline bool factorize_axis(int len, SmallAxis& ax) {
 struct lsp_plan_s {
   int device = 0;
   int d = 0, r = 0;
-  int64_t n[2] = {1, 1};
+  int64_t n[lsp::kMaxRank] = {1, 1, 1, 1};    // n_1..n_r, then 1
   int64_t ntot = 0;
   std::vector<int64_t> Z;        // d*r, row-major (component j of z_i at j*r + i)
   int prec = LSP_C64;
@@ -96,7 +100,7 @@ struct lsp_plan_s {
 
   // SMEM-resident geometry
   int naxes = 0;
-  lsp::SmallAxis axes[2];
+  lsp::SmallAxis axes[lsp::kMaxRank];
   int tw_lo = 0;              // complex64: offset of the lo parts of tw_small
 
   // device buffers

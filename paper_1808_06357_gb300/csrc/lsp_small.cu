@@ -29,7 +29,7 @@ template <typename T> struct SmallDesc {
   int tw_lo;         // offset of the lo parts (complex64)
   int n;
   int naxes;
-  SmallAxis axes[2];
+  SmallAxis axes[kMaxRank];
   R inv_n;           // 1/n rounded
   R inv_n_lo;        // 1/n - inv_n
   const T* twl;      // rank 1, n = 2^logn with a line kernel: its per-pass twiddles (else null)
@@ -234,8 +234,7 @@ template <typename T> static SmallDesc<T> make_small(lsp_plan p) {
   S.spec = (double2*)p->stage;
   S.n = (int)p->ntot;
   S.naxes = p->naxes;
-  S.axes[0] = p->axes[0];
-  S.axes[1] = p->axes[1];
+  for (int i = 0; i < kMaxRank; ++i) S.axes[i] = p->axes[i];
   S.inv_n = (decltype(S.inv_n))(1.0 / (double)p->ntot);
   S.inv_n_lo = (decltype(S.inv_n))(1.0 / (double)p->ntot - (double)S.inv_n);
   S.twl = (const T*)p->tw_pass;

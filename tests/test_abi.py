@@ -105,3 +105,17 @@ def test_noalloc_binding_refuses_unchecked_buffers():
     with pytest.raises(ValueError, match="CUDA tensor"):
         lsp.strang_steps_noalloc(torch.zeros(16, dtype=torch.complex64), torch.zeros(16, dtype=torch.float64),
                                  torch.zeros(16, dtype=torch.int32), 0.1, 1e-3, 1)
+
+
+def test_plan_create_rank_checks_before_any_device_call():
+    """Rank and canonical-form checks (Def. 1, Sec. 2.5) come before the device is touched, so
+    they answer the same with or without a GPU: r <= 4, and n_{i+1} divides n_i."""
+    import numpy as np
+    import pytest
+    import paper_1808_06357_gb300 as lsp
+    with pytest.raises(lsp.LspError) as e:                  # rank 5
+        lsp.Plan(np.eye(5, dtype=np.int64), (2, 2, 2, 2, 2), 0.1)
+    assert e.value.code == -1
+    with pytest.raises(lsp.LspError) as e:                  # 3 does not divide 8
+        lsp.Plan(np.eye(3, dtype=np.int64), (8, 3, 3), 0.1)
+    assert e.value.code == -2

@@ -12,7 +12,7 @@ import workloads as w
 pytestmark = pytest.mark.filterwarnings("ignore")
 
 # (Z, n) test lattices: the paper's worked example n=55, z=(1,34) (Sec. 2.1, Fig. 1),
-# small rank-1 lattices, a rank-2 lattice in canonical form and a regular grid.
+# small rank-1 lattices, rank-2 and rank-3 lattices in canonical form and regular grids.
 RANK1 = [
     (np.array([1, 34]), (55,)),
     (np.array([1, 5]), (32,)),
@@ -25,13 +25,19 @@ RANK2 = [
     (np.array([[1, 0], [5, 1], [7, 3]]), (16, 4)),
     (np.eye(2, dtype=np.int64), (8, 8)),            # regular grid (r = d, Z = I)
 ]
+# rank 3 (Sec. 2.5): seeded lattices whose N points are distinct (Def. 1), and a 3-D grid
+RANK3 = [
+    (np.array([[1, 0, 0], [1, 1, 6], [6, 4, 0], [0, 2, 3]]), (8, 4, 2)),
+    (np.array([[1, 0, 0], [0, 4, 4], [0, 0, 2], [2, 5, 3]]), (6, 6, 3)),
+    (np.eye(3, dtype=np.int64), (4, 4, 2)),
+]
 
 
 def _box(d, half):
     return np.array(list(itertools.product(range(-half, half + 1), repeat=d)), dtype=np.int64)
 
 
-@pytest.mark.parametrize("Z,n", RANK1 + RANK2)
+@pytest.mark.parametrize("Z,n", RANK1 + RANK2 + RANK3)
 def test_character_property(Z, n):
     """eq. char: (1/N) sum_p exp(2 pi i h.p) = 1 if h in the dual lattice, else 0."""
     P = L.lattice_points(Z, n)
@@ -48,7 +54,7 @@ def test_character_property(Z, n):
     assert np.allclose(s[~dual], 0.0, atol=1e-12)
 
 
-@pytest.mark.parametrize("Z,n", RANK1 + RANK2)
+@pytest.mark.parametrize("Z,n", RANK1 + RANK2 + RANK3)
 def test_points_distinct_and_canonical(Z, n):
     """Def. 1: a canonical lattice has prod n_i distinct points in [0,1)^d."""
     P = L.lattice_points(Z, n)
@@ -88,7 +94,7 @@ def _bruteforce_min_norms(Z, n, half):
     return best
 
 
-@pytest.mark.parametrize("Z,n", RANK1 + RANK2)
+@pytest.mark.parametrize("Z,n", RANK1 + RANK2 + RANK3)
 def test_minl2_dp_equals_paper_recipe_and_bruteforce(Z, n):
     """eq. hrepresenter: DP norms = the paper's sort-and-greedy recipe (Sec. 3.1) = exhaustive minimum."""
     N = int(np.prod(n))
@@ -151,7 +157,7 @@ def test_regular_grid_minl2_is_symmetric_box():
     assert np.array_equal(dp, exp)
 
 
-@pytest.mark.parametrize("Z,n", [RANK1[0], RANK1[2], RANK2[0]])
+@pytest.mark.parametrize("Z,n", [RANK1[0], RANK1[2], RANK2[0], RANK3[0], RANK3[1]])
 def test_dual_character_property(Z, n):
     """Thm 1(i): (1/N) sum_{h in A} exp(2 pi i h.(p - p')) = delta_{p,p'} for a full A."""
     dp, _ = L.minl2_norms_dp(Z, n)

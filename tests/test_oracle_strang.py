@@ -13,6 +13,7 @@ CASES = [
     (np.array([1, 34]), (55,)),                       # Sec. 2.1 worked example
     (np.array([1, 7, 11]), (64,)),
     (np.array([[1, 0], [3, 1]]), (12, 6)),            # rank-2, canonical
+    (np.array([[1, 0, 0], [1, 1, 6], [6, 4, 0], [0, 2, 3]]), (8, 4, 2)),   # rank-3 (Sec. 2.5), canonical
 ]
 
 
@@ -195,6 +196,30 @@ def test_regular_grid_equals_textbook_split_step():
         u = np.fft.ifft2(kin * np.fft.fft2(u))
         u = half * u
     # fftfreq puts the Nyquist wave number at -N/2; |h|^2 is the same for +-N/2
+    assert np.allclose(out, u.reshape(-1), atol=1e-12)
+
+
+def test_regular_3d_grid_equals_textbook_split_step():
+    """Rank-3 lattice with Z = I, n = (N, N, N/2) is a regular 3-D grid (Sec. 2.1, 2.5): the step is
+    the classic split-step Fourier method over a 3-D array, with fftfreq wave numbers."""
+    n = (8, 8, 4)
+    Z = np.eye(3, dtype=np.int64)
+    P = L.lattice_points(Z, n)
+    dp, _ = L.minl2_norms_dp(Z, n)
+    gamma, dt, steps = 0.15, 0.01, 20
+    v = w.v_harmonic(P)
+    u0 = w.gaussian_packet(P, 0.15, [0.45, 0.55, 0.5], k0=1)
+    out = S.strang(u0, v, dp, n, gamma, dt, steps)
+    k = [np.fft.fftfreq(m, d=1.0 / m) for m in n]
+    k2 = k[0][:, None, None] ** 2 + k[1][None, :, None] ** 2 + k[2][None, None, :] ** 2
+    kin = np.exp(-1j * gamma * 2 * np.pi ** 2 * k2 * dt)
+    half = np.exp(-1j * dt * v.reshape(n) / (2 * gamma))
+    u = u0.reshape(n)
+    for _ in range(steps):
+        u = half * u
+        u = np.fft.ifftn(kin * np.fft.fftn(u))
+        u = half * u
+    # the Nyquist wave number -N/2 of fftfreq has the same |h|^2 as +N/2
     assert np.allclose(out, u.reshape(-1), atol=1e-12)
 
 
