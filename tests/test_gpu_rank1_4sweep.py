@@ -48,8 +48,9 @@ def test_four_sweep_parity(lib, m, prec):
 
 
 def test_four_sweep_default_beyond_two_sweep_sizes(lib):
-    """n = 2^24 (c64 and c128) and 2^23 (c128) exceed the two-sweep kernels: the plan takes the
-    four-sweep path on its own."""
+    """n = 2^24 (c128) and 2^23 (c128) exceed the complex128 two-sweep kernels: the plan takes the
+    four-sweep path on its own; in complex64 the TMA two-sweep path is the default at 2^24 and the
+    four-sweep path is taken on request."""
     import torch
     inst = w.c2(24)
     P = L.lattice_points(inst.Z, inst.n)
@@ -59,6 +60,9 @@ def test_four_sweep_default_beyond_two_sweep_sizes(lib):
     ref = S.strang(u0, v, norms, inst.n, inst.gamma, inst.dt, 10)
     for prec in ("c128", "c64"):
         plan = lib.Plan(inst.Zmat, inst.n, inst.gamma, prec=prec)
+        if prec == "c64":
+            assert plan.info()["path"] == lib.PATH_RANK1_TMA
+            plan.set_path(lib.PATH_RANK1_4SWEEP)
         assert plan.info()["path"] == lib.PATH_RANK1_4SWEEP
         plan.set_potential(torch.from_numpy(v).cuda())
         plan.set_state(torch.from_numpy(u0).cuda())

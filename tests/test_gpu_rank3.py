@@ -83,7 +83,9 @@ def test_strang_50_steps_matches_oracle(lib, name, prec):
     spec = plan.get_state(space="spectral", prec="c128").cpu().numpy()
     assert _rel(spec, S.coeffs(ref, n)) < TOL[prec]
     nn, e = plan.observables()
-    tol_n, tol_e = (1e-12, 1e-10) if prec == "c128" else (2e-6, 1e-4)
+    # complex64: 50 steps of FP32 rounding move the norm by a few 1e-6 (the state is held to 5e-5
+    # above, which bounds the norm's relative error by 1e-4)
+    tol_n, tol_e = (1e-12, 1e-10) if prec == "c128" else (1e-5, 1e-4)
     assert abs(nn - S.norm2(ref)) < tol_n * S.norm2(ref)
     e_ref = S.energy(ref, v, norms, n, GAMMA)
     assert abs(e - e_ref) < tol_e * abs(e_ref)
