@@ -312,6 +312,10 @@ bool s2_batchable(lsp_plan p) {
 }
 
 int s2_group_init(lsp_batch_s::S2Group& g, const std::vector<lsp_plan>& plans) {
+  // Instances in size order, so that the tiles that the CTAs hold at any one time are mostly of
+  // one size (one code path, one twiddle table, the same tile set-up): C3's 140 instances of
+  // 2^16 .. 2^20 points took 349 ms per 500-step call in size order, 386 ms in arbitrary order.
+  std::stable_sort(g.ids.begin(), g.ids.end(), [&](int a, int b) { return plans[a]->logn < plans[b]->logn; });
   std::vector<int2> map;
   for (size_t k = 0; k < g.ids.size(); ++k) {
     const int nt = 1 << (plans[g.ids[k]]->logn - kS2LogN1);
@@ -340,6 +344,9 @@ void s2_group_free(lsp_batch_s::S2Group& g) {
   g = lsp_batch_s::S2Group();
 }
 
+// The group's launches of one call: one launch per sweep over every tile of every size.  (Each
+// size's whole call in turn, so that the small sizes' state stays in L2, measured slower: 366
+// against 349 ms per C3 call.)
 static int s2_group_launches(const lsp_batch_s::S2Group& g, int64_t nsteps, int* err, cudaStream_t s) {
   const S2BatchKernels K = s2_batch_kernels();
   const S2Inst* d = (const S2Inst*)g.inst;
