@@ -90,8 +90,8 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  * nothing is leaked.
  * The state starts at zero and the potential at v = 0.
  * Execution paths (the first available in this order is chosen: rank 1:
- * 0, 3, 1, 4, but for complex64 1, 3, 0, 4 at n = 2^13, 4, 3, 0, 1 from 2^20 to
- * 2^24 and 3, 0, 1, 4 above;
+ * 0, 3, 1, 4, 5, but for complex64 1, 3, 0, 4, 5 at n = 2^13, 4, 3, 0, 1, 5 from 2^20
+ * to 2^24 and 3, 0, 1, 4, 5 above;
  * rank 2: 1, 2; ranks 3 and 4: 1; reported by lsp_plan_info, changed by lsp_plan_set_path or
  * lsp_plan_autotune):
  *   0 multipass, rank 1: n = 2^m, 13 <= m <= 23 (complex64) or 22 (complex128);
@@ -102,7 +102,10 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *     (10, 8), (11, 9), (12, 10), (14, 12);
  *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25};
  *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 16 <= m <= 24
- *     (tiles of 4096 points on 256-thread CTAs; at 2^24 of 8192 points on 512 threads).
+ *     (tiles of 4096 points on 256-thread CTAs; at 2^24 of 8192 points on 512 threads);
+ *   5 two-sweep with mixed-radix line transforms, rank 1: any n = N1 N2 with
+ *     N2 <= N1 <= 4096 (eq. Fnx for n that is not a power of two; any radix per
+ *     factor, the four-step twiddle in FP64), chosen where no other path applies.
  * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
@@ -239,8 +242,9 @@ int lsp_plan_set_path(lsp_plan p, int path);
  * (lsp_autotune_cache) and reused by later plans of the same key without
  * timing.  Not in the paper: a schedule choice.
  *   chosen  receives the kept path (may be NULL).
- *   ms      NULL, or 5 doubles receiving each path's time in ms, its best schedule's
- *           for path 4 (-1: not available).
+ *   ms      NULL, or 6 doubles (one per execution path 0..5) receiving each path's
+ *           time in ms, its best schedule's for path 4 (-1: not available or not
+ *           timed; path 5 is timed only for plans that no other path takes).
  * Synchronises `stream`.  Errors: BAD_ARG, OOM, CUDA, TIMEOUT (then the plan
  * keeps the path it had).
  */

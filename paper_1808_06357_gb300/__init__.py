@@ -10,7 +10,7 @@ binding of that ABI.
 """
 
 from ._binding import (  # noqa: F401
-    AA_EXPLICIT, AA_MINL2, C64, C128, PATH_MULTIPASS, PATH_RANK1_4SWEEP, PATH_RANK1_TMA, PATH_RANK2, PATH_SMALL, PHYSICAL, SPECTRAL,
+    AA_EXPLICIT, AA_MINL2, C64, C128, PATH_MIXED, PATH_MULTIPASS, PATH_RANK1_4SWEEP, PATH_RANK1_TMA, PATH_RANK2, PATH_SMALL, PHYSICAL, SPECTRAL,
     Batch, LspError, Plan, adjoint, autotune_cache, cbc_reconstructing, fma_rate, library_path, load_library, strerror, strang_steps_noalloc,
     yoshida4,
 )

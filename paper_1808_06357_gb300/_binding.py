@@ -19,8 +19,8 @@ LSP_OK = 0
 C64, C128 = 1, 2
 AA_MINL2, AA_EXPLICIT = 0, 1
 PHYSICAL, SPECTRAL = 0, 1
-PATH_MULTIPASS, PATH_SMALL, PATH_RANK2, PATH_RANK1_4SWEEP, PATH_RANK1_TMA = 0, 1, 2, 3, 4
-NUM_PATHS = 5
+PATH_MULTIPASS, PATH_SMALL, PATH_RANK2, PATH_RANK1_4SWEEP, PATH_RANK1_TMA, PATH_MIXED = 0, 1, 2, 3, 4, 5
+NUM_PATHS = 6
 
 _lib = None
 _lock = threading.Lock()

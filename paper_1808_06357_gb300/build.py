@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "liblsp.so")
 SOURCES = ["lsp_api.cu", "lsp_small.cu", "lsp_batch.cu", "lsp_adjoint.cu", "lsp_mp_host.cu", "lsp_mp_c64_lo.cu", "lsp_mp_c64_hi.cu",
            "lsp_mp_c128_lo.cu", "lsp_mp_c128_hi.cu", "lsp_sweep4_host.cu", "lsp_sweep4_r2.cu", "lsp_sweep4_r1.cu", "lsp_cbc.cu", "lsp_peak.cu", "lsp_s2.cu",
            "lsp_s2_m16.cu", "lsp_s2_m17.cu", "lsp_s2_m18.cu", "lsp_s2_m19.cu", "lsp_s2_m20.cu", "lsp_s2_m21.cu",
-           "lsp_s2_m22.cu", "lsp_s2_m23.cu", "lsp_s2_m24.cu", "lsp_s2_batch.cu"]
+           "lsp_s2_m22.cu", "lsp_s2_m23.cu", "lsp_s2_m24.cu", "lsp_s2_batch.cu", "lsp_mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-strict-aliasing", "-I", INCLUDE, "-I", CSRC]

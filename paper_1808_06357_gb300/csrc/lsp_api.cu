@@ -203,7 +203,12 @@ __global__ void build_klut(T* lut, int count, double turns_k) {
 }
 
 // Bin chi held at position i of the K sweep's native order (identity for the SMEM path).
-__device__ __forceinline__ long long native_bin(long long i, int order, int logN1, int logN2) {
+__device__ __forceinline__ long long native_bin(long long i, int order, int logN1, int logN2, int N1 = 0,
+                                                int N2 = 0) {
+  if (order == kPathMixed) {       // position xi1 + N1 xi2 <- bin xi2 + N2 xi1 (any N1, N2)
+    const long long xi1 = i % N1, xi2 = i / N1;
+    return xi2 + (long long)N2 * xi1;
+  }
   if (order == kPathMultipass) {   // position xi1 + N1 xi2 <- bin xi2 + N2 xi1
     long long xi1 = i & ((1ll << logN1) - 1), xi2 = i >> logN1;
     return xi2 + (xi1 << logN2);
@@ -253,7 +258,7 @@ __host__ __device__ __forceinline__ long long s2_p_point(long long i, int logN2)
 template <typename T>
 __global__ void build_tables(const double* __restrict__ v, const int32_t* __restrict__ norm2, T* Ph, T* Pf, T* K,
                              const T* __restrict__ klut, long long n, double turns_v, double turns_k, int order,
-                             int logN1, int logN2) {
+                             int logN1, int logN2, int N1, int N2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long pk = order == kPathRank1x2 ? s2_p_point(i, logN2) : i;
     double th = v[pk] * turns_v;                      // -dt v / (4 pi gamma): half step, in turns
@@ -262,7 +267,7 @@ __global__ void build_tables(const double* __restrict__ v, const int32_t* __rest
     Ph[i] = a;
     Pf[i] = b;
     if (K) {
-      const long long bin = native_bin(i, order, logN1, logN2);
+      const long long bin = native_bin(i, order, logN1, logN2, N1, N2);
       if (klut) c = klut[norm2[bin]];
       else encode_phase(turns_k * (double)norm2[bin], &c);
       K[i] = c;
@@ -356,12 +361,12 @@ int build_phase_tables(lsp_plan p, double dt, cudaStream_t s) {
     if (nlut) build_klut<float2><<<(nlut + 255) / 256, 256, 0, s>>>((float2*)p->klut, nlut, turns_k);
     build_tables<float2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (float2*)p->Ph, (float2*)p->Pf,
                                                             (float2*)K, (const float2*)p->klut, p->ntot, turns_v,
-                                                            turns_k, order, p->logN1, p->logN2);
+                                                            turns_k, order, p->logN1, p->logN2, p->N1, p->N2);
   } else {
     if (nlut) build_klut<double2><<<(nlut + 255) / 256, 256, 0, s>>>((double2*)p->klut, nlut, turns_k);
     build_tables<double2><<<grid_for(p->ntot), 256, 0, s>>>(p->v, p->norm2, (double2*)p->Ph, (double2*)p->Pf,
                                                               (double2*)K, (const double2*)p->klut, p->ntot,
-                                                              turns_v, turns_k, order, p->logN1, p->logN2);
+                                                              turns_v, turns_k, order, p->logN1, p->logN2, p->N1, p->N2);
   }
   return cuda_status(cudaGetLastError());
 }
@@ -480,6 +485,10 @@ static bool path_available(lsp_plan p, int path) {
     case kPathMultipass: return p->r == 1 && logn >= 13 && multipass_supports(p->prec, logn);
     case kPathRank1x4: return p->r == 1 && logn > 0 && s4_supports_rank1(p->prec, logn);
     case kPathRank1x2: return p->r == 1 && logn > 0 && s2_supports(p->prec, logn);
+    case kPathMixed: {
+      int a = 0, b = 0;
+      return p->r == 1 && mixed_geometry(p->ntot, &a, &b);
+    }
     case kPathRank2: {
       const int m1 = ilog2exact(p->n[0]), m2 = ilog2exact(p->n[1]);
       return p->r == 2 && m1 > 0 && m2 > 0 && s4_supports_rank2(p->prec, m1, m2);
@@ -591,6 +600,37 @@ static int setup_path_tables(lsp_plan p, int path) {
     passes(tw, lb);
     return upload(p, &p->tw_pass, tw);
   }
+  if (path == kPathMixed) {
+    // rank 1, n = N1 N2 with mixed radices: per-axis pass tables in the SMEM-resident path's form
+    // (entries, then complex64's rounding residues), and FP64 tables of the four-step twiddle
+    int a = 0, b = 0;
+    if (!mixed_geometry(ntot, &a, &b)) return LSP_ERR_TOO_LARGE;
+    p->N1 = a; p->N2 = b; p->logN1 = p->logN2 = 0;
+    p->naxes = 2;
+    p->axes[0].len = a; p->axes[0].stride = 1;
+    p->axes[1].len = b; p->axes[1].stride = 1;
+    if (!factorize_axis(a, p->axes[0]) || !factorize_axis(b, p->axes[1])) return LSP_ERR_TOO_LARGE;
+    auto plain = [&](std::vector<unsigned char>& t, long long len, bool lo) {
+      if (prec == LSP_C64) fill_twiddles<float2>(t, len, len, lo, false);
+      else fill_twiddles<double2>(t, len, len, lo, false);
+    };
+    p->axes[0].tw_off = 0;
+    plain(tw, a, false);
+    p->axes[1].tw_off = (int)(tw.size() / sz);
+    plain(tw, b, false);
+    if (prec == LSP_C64) {
+      p->tw_lo = (int)(tw.size() / sz);
+      plain(tw, a, true);
+      plain(tw, b, true);
+    }
+    if ((rc = upload(p, &p->tw_small, tw))) return rc;
+    tw.clear();
+    fill_twiddles<double2>(tw, a, a, false, false);          // W_N1^q, q < N1
+    if ((rc = upload(p, &p->tw_coarse, tw))) return rc;
+    tw.clear();
+    fill_twiddles<double2>(tw, b, ntot, false, false);       // W_n^r, r < N2
+    return upload(p, &p->tw_fine, tw);
+  }
   // SMEM-resident path: per-axis mixed-radix tables
   p->naxes = p->r;
   long long stride = 1;
@@ -651,6 +691,7 @@ int path_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s) {
     case kPathMultipass: return multipass_steps_on(p, state, nsteps, s);
     case kPathSmall: return small_steps_on(p, state, nsteps, s);
     case kPathRank1x2: return s2_steps_on(p, state, nsteps, s);
+    case kPathMixed: return mixed_steps_on(p, state, nsteps, s);
     default: return s4_steps_on(p, state, nsteps, s);
   }
 }
@@ -661,6 +702,7 @@ static int path_spectral(lsp_plan p, cudaStream_t s) {
     case kPathMultipass: return multipass_spectral(p, s);
     case kPathSmall: return small_spectral(p, s);
     case kPathRank1x2: return s2_spectral(p, s);
+    case kPathMixed: return mixed_spectral(p, s);
     default: return s4_spectral(p, s);
   }
 }
@@ -736,15 +778,16 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   const bool four_first = prec == LSP_C64 && logn0 >= 20;
   const bool tma_first = prec == LSP_C64 && logn0 >= 20 && logn0 <= 24;
   const bool small_first = prec == LSP_C64 && r == 1 && logn0 == 13;
-  const int order_tma[] = {kPathRank1x2, kPathRank1x4, kPathMultipass, kPathSmall};
+  // the mixed-radix two-sweep path last: it is there for n that none of the others takes
+  const int order_tma[] = {kPathRank1x2, kPathRank1x4, kPathMultipass, kPathSmall, kPathMixed};
   const int order_rest[] = {small_first ? kPathSmall : four_first ? kPathRank1x4 : kPathMultipass,
                             four_first ? kPathMultipass : kPathRank1x4, small_first ? kPathMultipass : kPathSmall,
-                            kPathRank1x2};
+                            kPathRank1x2, kPathMixed};
   const int* order1 = tma_first ? order_tma : order_rest;
   const int order2[] = {kPathSmall, kPathRank2};
   int path = -1;
   if (r == 1) {
-    for (int k = 0; k < 4; ++k) if (path < 0 && path_available(p, order1[k])) path = order1[k];
+    for (int k = 0; k < 5; ++k) if (path < 0 && path_available(p, order1[k])) path = order1[k];
   } else {
     for (int c : order2) if (path < 0 && path_available(p, c)) path = c;
   }
@@ -1187,8 +1230,12 @@ int lsp_plan_autotune(lsp_plan p, double dt, int64_t nsteps, void* stream, int* 
   float best_ms = 0.f;
   TuneEntry entry;
   for (int c = 0; c < kNumPaths; ++c) entry.ms[c] = -1.0;
+  // the mixed-radix path is timed only when no other path takes the plan (it is the general
+  // fallback, slower than the specialised paths wherever they apply)
+  bool other = false;
+  for (int c = 0; c < kNumPaths; ++c) other = other || (c != kPathMixed && path_available(p, c));
   for (int c = 0; c < kNumPaths && !rc; ++c) {
-    if (!path_available(p, c)) continue;
+    if (!path_available(p, c) || (c == kPathMixed && other)) continue;
     if (c != p->path && (rc = setup_path(p, c))) break;
     // the TMA two-sweep path: every kernel schedule of the size
     const int nsched = c == kPathRank1x2 ? kS2NumScheds : 1;

@@ -115,7 +115,8 @@ int lsp_batch_create(lsp_batch* out, const lsp_plan* plans, int count) {
     if (plans[i]->path == kPathMultipass) by_m[plans[i]->logn].push_back(i);
     else if (s2_batchable(plans[i])) b->s2group.ids.push_back(i);
     else if (s4_batchable(plans[i])) by_m4[{plans[i]->logn, plans[i]->kidx != nullptr}].push_back(i);
-    else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4 || plans[i]->path == kPathRank1x2)
+    else if (plans[i]->path == kPathRank2 || plans[i]->path == kPathRank1x4 || plans[i]->path == kPathRank1x2 ||
+             plans[i]->path == kPathMixed)
       b->seq_ids.push_back(i);
     else by_line[small_line_logn(plans[i])].push_back(i);
   }

@@ -36,7 +36,10 @@ constexpr long long kSpinLimit = 1ll << 25;
 
 // Execution paths (lsp_plan_info [3]): rank-1 two-sweep multipass (persistent kernel),
 // SMEM-resident, rank-2 four-sweep, rank-1 four-sweep, rank-1 two-sweep with TMA-fed tiles.
-enum PathKind { kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2, kPathRank1x4 = 3, kPathRank1x2 = 4, kNumPaths = 5 };
+enum PathKind {
+  kPathMultipass = 0, kPathSmall = 1, kPathRank2 = 2, kPathRank1x4 = 3, kPathRank1x2 = 4, kPathMixed = 5,
+  kNumPaths = 6
+};
 
 // --------------------------------------------------------------------------
 // Plan
@@ -380,6 +383,11 @@ bool s2_supports(int prec, int m);
 int s2_upload_desc(lsp_plan p);                            // after the tables or the K form changed
 int s2_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
 int s2_spectral(lsp_plan p, cudaStream_t s);               // -> p->stage (chi order, c128)
+
+// mixed-radix two-sweep path (rank 1, n = N1 N2 with N2 <= N1 <= 4096)
+bool mixed_geometry(long long n, int* N1, int* N2);
+int mixed_steps_on(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s);
+int mixed_spectral(lsp_plan p, cudaStream_t s);            // -> p->stage (chi order, c128)
 int s2_sweep_times(lsp_plan p, void* state, int64_t nsteps, cudaStream_t s, double* ms);
 bool s2_batchable(lsp_plan p);
 int s2_group_init(lsp_batch_s::S2Group& g, const std::vector<lsp_plan>& plans);

@@ -15,6 +15,7 @@
 
 #include "lsp_internal.cuh"
 #include "lsp_tile.cuh"
+#include "lsp_pass.cuh"
 
 namespace lsp {
 
@@ -35,47 +36,6 @@ template <typename T> struct SmallDesc {
   const T* twl;      // rank 1, n = 2^logn with a line kernel: its per-pass twiddles (else null)
   int logn;
 };
-
-template <int DIR, typename T>
-__device__ void small_pass(const SmallAxis& ax, const T* tw, int tw_lo, int R, int Ns, int n, const T* x, T* y) {
-  const int len = ax.len, st = ax.stride;
-  const int m = len / (Ns * R);          // len / (Ns R)
-  const int lenR = len / R;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int inner = e % st;
-    const int ia = (e / st) % len;
-    const int outer = e / (st * len);
-    const int jm = ia % Ns;
-    const int s = (ia / Ns) % R;
-    const int j = (ia / (Ns * R)) * Ns + jm;
-    const int base = outer * st * len + inner;
-    const int step = jm + Ns * s;
-    T acc;
-    acc.x = 0;
-    acc.y = 0;
-    int kk = 0;                            // (r * step) mod (Ns R)
-    const int NsR = Ns * R;
-    for (int r = 0; r < R; ++r) {
-      T xv = x[base + (j + r * lenR) * st];
-      T w = __ldg(tw + ax.tw_off + kk * m);
-      if (DIR > 0) w.y = -w.y;
-      if constexpr (sizeof(T) == 8) {
-        // FP32: twiddle as hi + lo so the fixed rounding of each table entry
-        // does not accumulate over the steps
-        T wl = __ldg(tw + tw_lo + ax.tw_off + kk * m);
-        if (DIR > 0) wl.y = -wl.y;
-        const float tr = fmaf(xv.x, wl.x, -xv.y * wl.y), ti = fmaf(xv.x, wl.y, xv.y * wl.x);
-        acc.x = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, acc.x + tr));
-        acc.y = fmaf(xv.x, w.y, fmaf(xv.y, w.x, acc.y + ti));
-      } else {
-        acc = cadd(acc, cmul(xv, w));
-      }
-      kk += step;
-      if (kk >= NsR) kk -= NsR;
-    }
-    y[e] = acc;
-  }
-}
 
 // Full r-D DFT (DIR = -1 forward, +1 inverse, unnormalised); returns the buffer with the result.
 template <int DIR, typename T>
