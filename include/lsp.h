@@ -103,9 +103,9 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *   3 four-sweep, rank 1: n = 2^m, m in {20, 22, 23, 24, 25};
  *   4 two-sweep with TMA-fed tiles, rank 1, complex64: n = 2^m, 16 <= m <= 24
  *     (tiles of 4096 points on 256-thread CTAs; at 2^24 of 8192 points on 512 threads);
- *   5 two-sweep with mixed-radix line transforms, rank 1: any n = N1 N2 with
- *     N2 <= N1 <= 4096 (eq. Fnx for n that is not a power of two; any radix per
- *     factor, the four-step twiddle in FP64), chosen where no other path applies.
+ *   5 two-sweep with mixed-radix line transforms, rank 1: n not a power of two,
+ *     n = N1 N2 with N2 <= N1 <= 4096 (eq. Fnx; any radix per factor, the four-step
+ *     twiddle in FP64), chosen where no other path applies.
  * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,

@@ -70,13 +70,15 @@ def test_mixed_radix_50_steps_matches_oracle(lib, n, d, prec):
     plan.destroy()
 
 
-def test_mixed_radix_on_a_power_of_two_size(lib):
-    """The path takes any n = N1 N2 with factors up to 4096; on request it runs 2^16 too."""
-    n = 1 << 16
+def test_mixed_radix_on_request_where_the_smem_path_applies(lib):
+    """n = 2^12 3 fits the SMEM-resident path (the default there); the mixed-radix path runs it
+    on request; power-of-two sizes, which have the butterfly paths, are not offered to it."""
+    n = 12288
     z = _lattice(n, 3)
     P, v, u0 = _inputs(z, n)
     plan = _plan(lib, z, n, "c64", v, u0)
-    assert lib.PATH_MIXED in plan.paths()
+    assert plan.info()["path"] == lib.PATH_SMALL and lib.PATH_MIXED in plan.paths()
+    assert lib.PATH_MIXED not in lib.Plan(_lattice(1 << 16, 3), (1 << 16,), GAMMA, prec="c64").paths()
     plan.set_path(lib.PATH_MIXED)
     plan.strang_steps(DT, 20)
     assert plan.status() == 0
