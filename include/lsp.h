@@ -106,7 +106,7 @@ enum { LSP_SPACE_PHYSICAL = 0, LSP_SPACE_SPECTRAL = 1 };
  *   5 two-sweep with mixed-radix line transforms, rank 1: n not a power of two,
  *     n = N1 N2 with N2 <= N1 <= 4096 (eq. Fnx; any radix per factor, the four-step
  *     twiddle in FP64), chosen where no other path applies.
- * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (rank 2).
+ * Other sizes: TOO_LARGE (rank 1) or UNSUPPORTED (ranks 2 to 4).
  */
 int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t* Z,
                     const int32_t* index_set, int64_t m, int aa_mode, int prec,
@@ -204,8 +204,8 @@ int lsp_index_table(lsp_plan p, int32_t* h);
  * lsp_plan_info -- plan geometry, 8 int64 values (host):
  *   [0] n  [1] N1 (row length)  [2] N2 (column length)  [3] path (LSP_PATH_*)
  *   [4] precision  [5] device bytes held  [6] MINL2 DP box half-width (0 for
- *   EXPLICIT)  [7] max ||h_chi||^2.  For rank 2, N1 = n_2 (contiguous rows)
- *   and N2 = n_1.
+ *   EXPLICIT)  [7] max ||h_chi||^2.  For rank r >= 2, N1 = n_r (contiguous
+ *   rows) and N2 = n / n_r (on the rank-2 four-sweep path, N2 = n_1).
  */
 int lsp_plan_info(lsp_plan p, int64_t* info);
 
@@ -215,7 +215,8 @@ enum {
   LSP_PATH_SMEM = 1,           /* whole run in shared memory, one CTA per instance                 */
   LSP_PATH_RANK2 = 2,          /* rank-2, 2^m1 x 2^m2: four sweeps per step                        */
   LSP_PATH_RANK1_4SWEEP = 3,   /* rank-1, n = 2^m: four sweeps per step (rows of 4096 points)      */
-  LSP_PATH_RANK1_TMA = 4       /* rank-1, n = 2^m: two sweeps per step, tiles brought in by TMA    */
+  LSP_PATH_RANK1_TMA = 4,      /* rank-1, n = 2^m: two sweeps per step, tiles brought in by TMA    */
+  LSP_PATH_MIXED = 5           /* rank-1, n not a power of two: two sweeps, mixed-radix lines      */
 };
 
 /*
