@@ -151,8 +151,10 @@ template <> struct Swz<float2, 3> {
 template <> struct Swz<double2, 0> {  // 8 x 16 B per 128 B bank row
   static __device__ __forceinline__ int f(int e) { return e ^ ((e >> 3) & 7); }
 };
-// SW for a complex64 column line of 2^LOGL points on 256 threads
-constexpr int col_swizzle(int logl) { return logl == 11 ? 2 : logl == 9 ? 3 : 1; }
+// SW for a complex64 column line of 2^LOGL points on 256 threads; the 4096-point column lines
+// (two per tile, 512 threads) take SW = 0, the one conflict-free there (SW = 1 costs 1.75x the
+// minimum wavefronts by the same model)
+constexpr int col_swizzle(int logl) { return logl == 12 ? 0 : logl == 11 ? 2 : logl == 9 ? 3 : 1; }
 // Each swizzle changes only bits 0..3 (float2; 0..2 for double2) as a function of the bits
 // below its granule: f(e + OFF) = f(e) + OFF for every OFF that is a multiple of the granule.
 template <typename T, int SW> struct SwzGranule;
