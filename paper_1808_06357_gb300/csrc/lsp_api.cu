@@ -776,7 +776,7 @@ int lsp_plan_create(lsp_plan* out, int d, int r, const int64_t* n, const int64_t
   const int logn0 = ilog2exact(ntot);
   // complex64 from 2^20 to 2^24 points: the TMA-fed two-sweep path measured faster than both
   // (G point-steps/s, 100-step calls: 61.6 against 42.1 at 2^20, 79.2 against 55.7 at 2^22,
-  // 73.0 against 54.2 at 2^23, 64.9 against 55.0 at 2^24)
+  // 73.0 against 54.2 at 2^23, 68.4 against 55.0 at 2^24)
   const bool four_first = prec == LSP_C64 && logn0 >= 20;
   const bool tma_first = prec == LSP_C64 && logn0 >= 20 && logn0 <= 24;
   const bool small_first = prec == LSP_C64 && r == 1 && logn0 == 13;
